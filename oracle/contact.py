@@ -1,0 +1,206 @@
+"""Contact solves on top of the discrete operator (Sec. 2, inverse problem and adhesion).
+
+Test infrastructure (see ``oracle/__init__``).  Plain FP64 numpy; ``matvec`` is any
+callable p -> K p (``operator.matvec_fft`` or ``operator.matvec_dense`` bound to a
+sampled kernel).
+
+Conventions (Sec. 2, condition (c)): p > 0 is compressive, tension is p < 0; u is the
+surface displacement into the body; f is the indenter height above its lowest
+point; d is the indentation depth; the gap is g = u + f - d.  Non-adhesive contact
+(Sec. 2, "inverse problem ... conjugate gradient method as described in [8]") means
+p >= 0, g >= 0, p g = 0; the total force is F = delta^2 sum p.
+
+* ``solve_nonadhesive``  Polonsky-Keer constrained conjugate gradients, the method
+  the paper cites as [8], under depth control (d given) or load control (F given,
+  d is the multiplier).  Two operator products per iteration, written plainly.
+* ``kkt_violation``      complementarity check of a computed solution.
+* ``sigma_c``            Eq. (12), the mesh-dependent detachment stress.
+* ``boundary_cells``     cells of a contact set with a 4-neighbour outside it (the
+  window edge counts as outside) - the "elements at the boundary" of Sec. 2.
+* ``solve_fixed_set``    the inverse problem on a fixed contact area, p free in sign.
+* ``adhesive_step``      one displacement-controlled step of Sec. 2's adhesive
+  procedure: solve on the fixed area, add penetrating cells, detach boundary cells
+  whose tension exceeds sigma_c (all at once), repeat until the area is unchanged.
+* ``adhesive_ramp``      a sequence of such steps over a list of depths.
+
+Parity status: pinned by tests (KKT, NNLS brute force, Hertz, flat punch, thin
+layer, JKR, Eq. 16) - see tests/test_oracle_contact.py.
+"""
+import numpy as np
+
+
+class NoConvergence(RuntimeError):
+    pass
+
+
+def _initial_depth_control(matvec, f, d):
+    q = np.maximum(d - f, 0.0)
+    if not np.any(q > 0):
+        return np.zeros_like(f)
+    Kq = matvec(q)
+    s = np.sum(q * (d - f)) / np.sum(q * Kq)
+    return s * q
+
+
+def solve_nonadhesive(matvec, f, delta, control="depth", target=0.0, tol=1e-12,
+                      max_iter=20000, p0=None):
+    """Polonsky-Keer CG.  Returns dict(p, d, force, iters, residual, n_contact).
+
+    Iteration (depth control drops the mean shifts and the load rescale):
+      Ic = {p > 0};  u = K p;  g = u + f - d
+      load control: gbar = mean_Ic g;  g -= gbar;  d += gbar
+      G = sum_Ic g^2;  t = g + delta_flag (G/G_old) t on Ic, 0 elsewhere
+      r = K t;  load control: r -= mean_Ic r on Ic
+      tau = sum_Ic g t / sum_Ic r t
+      p -= tau t on Ic;  p[p < 0] = 0
+      Iol = {p = 0, g < 0}: delta_flag = 0 and p -= tau g on Iol if Iol non-empty
+      load control: p *= F / (delta^2 sum p)
+    Stop at the start of an iteration when sqrt(G)/||u||_Ic <= tol and the previous
+    iteration changed no cell of the contact set.
+    """
+    f = np.asarray(f, dtype=np.float64)
+    load = control == "force"
+    if load:
+        W = float(target)
+        d = 0.0
+        p = np.full_like(f, W / (delta * delta * f.size)) if p0 is None else np.array(p0, dtype=np.float64)
+        p *= W / (delta * delta * p.sum())
+    else:
+        d = float(target)
+        p = _initial_depth_control(matvec, f, d) if p0 is None else np.maximum(np.array(p0, dtype=np.float64), 0.0)
+    t = np.zeros_like(f)
+    G_old = 1.0
+    flag = 0.0
+    set_changed = True
+    res = np.inf
+    for it in range(1, max_iter + 1):
+        Ic = p > 0
+        if not np.any(Ic):
+            if load:
+                raise NoConvergence("empty contact set under load control")
+            return dict(p=p, d=d, force=0.0, iters=it - 1, residual=0.0, n_contact=0)
+        u = matvec(p)
+        g = u + f - d
+        if load:
+            gbar = g[Ic].mean()
+            g -= gbar
+            d += gbar
+        G = np.sum(g[Ic] ** 2)
+        unorm = np.sqrt(np.sum(u[Ic] ** 2))
+        res = np.sqrt(G) / unorm if unorm > 0 else 0.0
+        if res <= tol and not set_changed:
+            return dict(p=p, d=d, force=delta * delta * p.sum(), iters=it - 1,
+                        residual=res, n_contact=int(Ic.sum()))
+        t = np.where(Ic, g + flag * (G / G_old) * t, 0.0)
+        G_old = G
+        r = matvec(t)
+        if load:
+            r[Ic] -= r[Ic].mean()
+        tau = np.sum(g[Ic] * t[Ic]) / np.sum(r[Ic] * t[Ic])
+        p = np.where(Ic, p - tau * t, p)
+        neg = p < 0
+        p[neg] = 0.0
+        Iol = (p == 0) & (g < 0)
+        if np.any(Iol):
+            flag = 0.0
+            p[Iol] -= tau * g[Iol]
+        else:
+            flag = 1.0
+        set_changed = bool(np.any(neg) or np.any(Iol))
+        if load:
+            p *= W / (delta * delta * p.sum())
+    raise NoConvergence(f"PK-CG: residual {res:.3e} after {max_iter} iterations")
+
+
+def kkt_violation(matvec, p, f, d):
+    """Max violation of p >= 0, g >= 0, p g = 0 relative to max|u| (and the tension)."""
+    u = matvec(p)
+    g = u + f - d
+    scale = max(np.abs(u).max(), 1e-300)
+    pscale = max(np.abs(p).max(), 1e-300)
+    v_p = max(0.0, -p.min()) / pscale
+    v_g = max(0.0, -g.min()) / scale
+    v_c = np.abs(g[p > 0]).max() / scale if np.any(p > 0) else 0.0
+    return max(v_p, v_g, v_c)
+
+
+def sigma_c(E1, nu1, dgamma, delta):
+    """Eq. (12): sqrt(E1* dgamma / (0.473201 delta)), E1* = E1/(1-nu1^2)."""
+    return np.sqrt(E1 / (1.0 - nu1 * nu1) * dgamma / (0.473201 * delta))
+
+
+def boundary_cells(C):
+    """Cells of C with at least one von Neumann neighbour outside C (window edge = outside)."""
+    pad = np.zeros((C.shape[0] + 2, C.shape[1] + 2), dtype=bool)
+    pad[1:-1, 1:-1] = C
+    inner = pad[:-2, 1:-1] & pad[2:, 1:-1] & pad[1:-1, :-2] & pad[1:-1, 2:]
+    return C & ~inner
+
+
+def solve_fixed_set(matvec, C, b, tol=1e-13, max_iter=20000, p0=None):
+    """Plain CG for K_CC p_C = b_C with p = 0 outside C (p unrestricted in sign)."""
+    p = np.zeros_like(b) if p0 is None else np.where(C, p0, 0.0)
+    r = np.where(C, b - matvec(p), 0.0)
+    bnorm = np.sqrt(np.sum(b[C] ** 2))
+    if bnorm == 0.0:
+        return np.zeros_like(b), 0
+    s = r.copy()
+    rr = np.sum(r * r)
+    for it in range(max_iter):
+        if np.sqrt(rr) <= tol * bnorm:
+            return p, it
+        Ks = np.where(C, matvec(s), 0.0)
+        a = rr / np.sum(s * Ks)
+        p = p + a * s
+        r = r - a * Ks
+        rr_new = np.sum(r * r)
+        s = r + (rr_new / rr) * s
+        rr = rr_new
+    raise NoConvergence("fixed-set CG did not converge")
+
+
+def adhesive_step(matvec, f, d, C, sig_c, p_prev=None, tol=1e-13, max_outer=1000):
+    """One displacement-controlled step of the adhesive procedure of Sec. 2.
+
+    With the contact area C held fixed the pressure that gives u = d - f on C is
+    found (p free in sign); cells outside C that penetrate (g < 0) join; boundary
+    cells of C whose tension -p exceeds sigma_c (Eq. 12, strict '>') leave, all at
+    once; this repeats until the area does not change.  Returns (p, C, outer, cg_iters).
+    """
+    C = C.copy()
+    seen = set()
+    p = p_prev
+    total = 0
+    for outer in range(1, max_outer + 1):
+        p, its = solve_fixed_set(matvec, C, d - f, tol=tol, p0=p)
+        total += its
+        g = matvec(p) + f - d
+        add = ~C & (g < 0)
+        detach = boundary_cells(C) & (-p > sig_c)
+        if not np.any(add) and not np.any(detach):
+            return p, C, outer, total
+        key = (C | add) & ~detach
+        h = key.tobytes()
+        if h in seen:
+            raise NoConvergence("contact set cycles")
+        seen.add(h)
+        C = key
+    raise NoConvergence("adhesive outer loop did not settle")
+
+
+def adhesive_ramp(matvec, f, delta, depths, sig_c, C0=None, tol=1e-13):
+    """Run ``adhesive_step`` over the given depths, carrying (p, C) between steps.
+
+    Returns a list of dicts with d, force = delta^2 sum p, n_contact and the
+    equivalent contact radius a_eq = sqrt(n delta^2 / pi).
+    """
+    C = np.zeros(f.shape, dtype=bool) if C0 is None else C0.copy()
+    p = None
+    out = []
+    for d in depths:
+        p, C, outer, its = adhesive_step(matvec, f, d, C, sig_c, p_prev=p, tol=tol)
+        n = int(C.sum())
+        out.append(dict(d=float(d), force=float(delta * delta * p.sum()), n_contact=n,
+                        a_eq=float(np.sqrt(n * delta * delta / np.pi)), outer=outer,
+                        cg_iters=its, p=p.copy(), C=C.copy()))
+    return out

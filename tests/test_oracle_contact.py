@@ -1,0 +1,140 @@
+"""Pins of the oracle's contact solvers against brute force and the paper's closed forms.
+
+Solution-level pins hold within discretisation error, so each tolerance is set from
+the grid (stated per test); the thick-layer test shows the pin is sharp by checking
+that plain Hertz (no layer correction) would fail it.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import brentq, nnls
+
+from oracle import analytic, contact, kernel, operator
+from paper_1807_01885_gb300 import inputs
+
+
+def _mv(N, delta, h, E1, nu1, E2, nu2, dc_mode=0):
+    Kg = operator.khat_grid(N, delta, h, E1, nu1, E2, nu2, dc_mode)
+    return Kg, (lambda p: operator.matvec_fft(Kg, p))
+
+
+def test_pk_matches_nnls_brute_force():
+    """Depth control is the QP min 1/2 p'Kp - p'(d - f), p >= 0; with K = L L' it is
+    the NNLS problem min ||L' p - L^{-1}(d - f)||, solved by an active-set library
+    routine that shares nothing with the CG."""
+    N, delta = 8, 0.1
+    Kg, mv = _mv(N, delta, 0.15, 2.0, 0.3, 1.0, 0.4)
+    Km = operator.dense_matrix(Kg)
+    f = inputs.sphere_height(N, delta, 0.5) + 0.002 * np.random.default_rng(3).standard_normal((N, N))
+    f -= f.min()
+    d = 0.02
+    Lc = np.linalg.cholesky(Km)
+    b = np.linalg.solve(Lc, (d - f).reshape(-1))
+    p_ref, _ = nnls(Lc.T, b, maxiter=10000)
+    s = contact.solve_nonadhesive(mv, f, delta, "depth", d, tol=1e-13)
+    np.testing.assert_allclose(s["p"].reshape(-1), p_ref, atol=1e-9 * p_ref.max())
+    assert contact.kkt_violation(mv, s["p"], f, d) < 1e-11
+
+
+def test_load_control_equals_depth_control():
+    N, delta = 32, 0.05
+    _, mv = _mv(N, delta, 0.2, 0.5, 0.3, 1.0, 0.45)
+    f = inputs.rough_surface(N, delta, seed=11)
+    s1 = contact.solve_nonadhesive(mv, f, delta, "force", 2e-3, tol=1e-13)
+    assert s1["force"] == pytest.approx(2e-3, rel=1e-12)
+    s2 = contact.solve_nonadhesive(mv, f, delta, "depth", s1["d"], tol=1e-13)
+    np.testing.assert_allclose(s2["p"], s1["p"], atol=1e-9 * s1["p"].max())
+    assert contact.kkt_violation(mv, s1["p"], f, s1["d"]) < 1e-10
+
+
+def test_hertz_homogeneous_load_control():
+    """E1 = E2: Hertz contact radius a = (3FR/4E*)^(1/3) and pressure
+    p0 sqrt(1 - r^2/a^2) (Eq. 22 at epsilon = 0, no adhesion).  Load control keeps
+    the result free of the DC offset of the periodic operator.  a = 16 cells."""
+    N, R, E, nu = 64, 1.0, 1.0, 0.3
+    aH = 0.1
+    delta = 4 * aH / N
+    Es = kernel.e_star(E, nu)
+    _, mv = _mv(N, delta, np.inf, E, nu, E, nu)
+    f = inputs.sphere_height(N, delta, R)
+    F = analytic.hertz(aH, R, Es)[0]
+    s = contact.solve_nonadhesive(mv, f, delta, "force", F, tol=1e-12)
+    a_num = np.sqrt(s["n_contact"] * delta ** 2 / np.pi)
+    assert a_num == pytest.approx(aH, rel=0.02)
+    x, y = inputs.cell_centres(N, delta)
+    ph = analytic.hertz_pressure(np.hypot(x, y), aH, R, Es)
+    assert np.linalg.norm(s["p"] - ph) / np.linalg.norm(ph) < 0.02
+
+
+@pytest.mark.parametrize("a_over_h,tol", [(10, 0.03), (20, 0.01)])
+def test_thin_layer_flat_punch_stiffness(a_over_h, tol):
+    """Rigid base, a >> h: k = pi a^2 E~1 / h (Eqs. 14/15).  Edge effects are
+    O(h/a), so the tolerance tightens as a/h grows."""
+    N, delta, E1, nu1 = 128, 1.0, 1.0, 0.3
+    a = N / 4
+    h = a / a_over_h
+    _, mv = _mv(N, delta, h, E1, nu1, np.inf, 0.3)
+    f = inputs.flat_punch_height(N, delta, a)
+    d = 1e-3
+    s = contact.solve_nonadhesive(mv, f, delta, "depth", d, tol=1e-12)
+    a_eff = np.sqrt(s["n_contact"] / np.pi) * delta
+    assert s["force"] / d == pytest.approx(analytic.thin_layer_stiffness(a_eff, h, E1, nu1), rel=tol)
+
+
+@pytest.mark.parametrize("h", [32.0, 64.0])
+def test_thick_layer_series_eq22_23(h):
+    """Rigid base, a < h: F(d) from Eqs. (22)/(23) at dgamma = 0, with a0, a1 of
+    Eq. (24).  The layer correction is 10-40 % here, so Hertz alone fails."""
+    N, delta, R, E1, nu1 = 128, 1.0, 400.0, 1.0, 0.3
+    Es = kernel.e_star(E1, nu1)
+    _, mv = _mv(N, delta, h, E1, nu1, np.inf, 0.3)
+    f = inputs.sphere_height(N, delta, R)
+    for d in (0.1, 0.2):
+        s = contact.solve_nonadhesive(mv, f, delta, "depth", d, tol=1e-11)
+        a = brentq(lambda a: analytic.thick_layer_sphere(a, R, h, E1, nu1, 0.0)[1] - d, 1e-3, h)
+        F_ser = analytic.thick_layer_sphere(a, R, h, E1, nu1, 0.0)[0]
+        F_hertz = 4.0 / 3.0 * Es * np.sqrt(R) * d ** 1.5
+        assert s["force"] == pytest.approx(F_ser, rel=5e-3)
+        assert abs(s["force"] / F_hertz - 1) > 0.05
+
+
+def test_boundary_cells():
+    C = np.zeros((6, 6), dtype=bool)
+    C[1:5, 1:5] = True
+    B = contact.boundary_cells(C)
+    assert B.sum() == 12 and not B[2, 2] and not B[3, 3] and B[1, 1] and B[4, 2]
+    full = np.ones((3, 3), dtype=bool)
+    assert contact.boundary_cells(full).sum() == 8     # the window edge counts as outside
+
+
+def test_jkr_pull_off_homogeneous():
+    """E1 = E2, displacement-controlled pull-off with the criterion of Eq. (12):
+    the force minimum approaches the JKR value -(3/2) pi R dgamma (minimum of F(a)
+    from Eqs. 22/23 at epsilon = 0) and the contact recedes before the jump-off
+    (the JKR jump-off radius is 5 cells here, the force minimum at 10)."""
+    N, R, E, nu = 64, 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Es = kernel.e_star(E, nu)
+    a_d = 5 * delta
+    dg = a_d ** 3 * 8 * Es / (np.pi * R * R)
+    a_F = 9 ** (1 / 3) * a_d
+    _, mv = _mv(N, delta, np.inf, E, nu, E, nu)
+    f = inputs.sphere_height(N, delta, R)
+    sc = contact.sigma_c(E, nu, dg, delta)
+    d_max = (1.4 * a_F) ** 2 / R
+    d_jump = analytic.jkr_jump_off(R, Es, dg)[2]
+    depths = np.concatenate([np.linspace(0, d_max, 6), np.linspace(d_max, 1.3 * d_jump, 60)])
+    out = contact.adhesive_ramp(mv, f, delta, depths, sc, tol=1e-10)
+    Fmin = min(o["force"] for o in out)
+    assert Fmin / analytic.jkr_pull_off_force(R, dg) == pytest.approx(1.0, abs=0.15)
+    n = [o["n_contact"] for o in out[6:]]
+    assert n[-1] == 0 and max(n) > 3 * min(x for x in n if x > 0)
+
+
+def test_sigma_c_constant_from_paper():
+    """Eq. (12) with the printed constant 0.473201 (tests/golden/paper_parameters.json)."""
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")))
+    c = g["eq12_constant"]["value"]
+    E1, nu1, dg, delta = 2.0, 0.3, 0.01, 0.05
+    s = contact.sigma_c(E1, nu1, dg, delta)
+    assert s * s * c * delta == pytest.approx(E1 / (1 - nu1 ** 2) * dg, rel=1e-14)
