@@ -1,0 +1,162 @@
+/*
+ * bem.h - C ABI of the GB300 FFT-BEM library (libbem.so).
+ *
+ * Contact of a rigid indenter with an elastic layer (thickness h, modulus E1,
+ * Poisson ratio nu1) bonded to an elastic half-space (E2, nu2), after
+ * Li, Pohrt, Lyashenko and Popov, "Boundary Element Method for non-adhesive and
+ * adhesive contacts of a coated elastic half-space" (arXiv:1807.01885).
+ *
+ * Discretisation (Sec. 2, Fig. 2): a square window of N x N cells of side delta,
+ * pressure uniform per cell, stored row-major (cell (r, c) at index r*N + c).
+ * The surface operator u = K p (Eq. 1) is evaluated as in Eq. (11):
+ *     u = crop( IFFT[ K^(|k|) . FFT(pad(p)) ] )
+ * on a 2N x 2N period (zero pressure outside the window), with the compliance
+ * K^(k) of Eq. (9)/(10) sampled at k = 2 pi (i, j) / (2N delta).  The k = 0 term,
+ * which Eq. (11) leaves undefined ("no DC component", Sec. 2), is the finite part
+ * lim_{k->0} [K^(k) - 2/(E2* k)] (dc_mode 0; equal to h/E~1 of Eq. 15 for a
+ * rigid base and to 0 for a homogeneous body) or 0 (dc_mode 1).
+ *
+ * Sign conventions (Sec. 2, condition (c)): p > 0 is compressive; u > 0 points
+ * into the body; the indenter height f >= 0 is measured up from its lowest
+ * point; d is the indentation depth; the gap is g = u + f - d.
+ *
+ * Memory: every array argument is a plain pointer to N*N elements of the kernel's
+ * precision (double for BEM_FP64, float for BEM_FP32), row-major, owned by the
+ * caller.  A pointer may be device memory or host memory (pageable or pinned);
+ * host arrays are staged through the library's own device workspace.  The library
+ * owns kernel handles and their workspaces.  No call throws; every call returns a
+ * bem_status and bem_last_error() gives a message for the calling thread.
+ * Calls on one handle must not overlap (the handle's workspace is shared).
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BEM_OK = 0,
+  BEM_EINVAL = 1,        /* invalid argument (null pointer, nu >= 0.5, h < 0, N not supported...) */
+  BEM_ENOMEM = 2,        /* device allocation failed */
+  BEM_ECUDA = 3,         /* a CUDA runtime call failed */
+  BEM_ENOCONV = 4,       /* iteration limit reached before the tolerance */
+  BEM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  BEM_ENAN = 6,          /* non-finite value met in a reduction */
+  BEM_ECYCLE = 7,        /* adhesive contact set revisited an earlier state */
+  BEM_EUNSUPPORTED = 8
+} bem_status;
+
+enum { BEM_FP64 = 0, BEM_FP32 = 1 };                   /* bem_kernel_desc.precision */
+enum { BEM_CTRL_DEPTH = 0, BEM_CTRL_FORCE = 1 };       /* bem_problem.control */
+enum { BEM_DC_FINITE_PART = 0, BEM_DC_ZERO = 1 };      /* bem_kernel_desc.dc_mode */
+
+/* Parameters of the discretised operator (Sec. 2): grid, cell size, layer and
+ * substrate.  N is a power of two, 4 <= N <= 2048.  h may be INFINITY (homogeneous
+ * E1, nu1), E2 may be INFINITY (rigid base; the paper's E2 = e^100).  0 <= nu < 0.5. */
+typedef struct {
+  int32_t N;
+  int32_t precision;    /* BEM_FP64: everything in double.  BEM_FP32: FFTs and vectors
+                           in float; reductions, CG scalars and the detachment
+                           test in double. */
+  int32_t dc_mode;
+  int32_t reserved;
+  double delta, h, E1, nu1, E2, nu2;
+} bem_kernel_desc;
+
+typedef struct bem_kernel_s* bem_kernel;
+
+/* One contact problem on a kernel's grid.
+ *  height        indenter height map f (N*N), host or device.
+ *  control       BEM_CTRL_DEPTH: target is the depth d.  BEM_CTRL_FORCE: target is
+ *                the total force F = delta^2 sum p (non-adhesive only).
+ *  dgamma        work of adhesion; 0 selects non-adhesive contact (p >= 0).  > 0
+ *                runs ONE displacement-controlled step of the adhesive procedure of
+ *                Sec. 2 at depth target, with the detachment stress of Eq. (12).
+ *  tol           relative gap residual ||g||_C / ||u||_C at which CG stops.
+ *  max_iter      CG iteration limit (per inner solve in adhesive mode).
+ *  p_init        optional warm start (N*N), may be NULL.
+ *  contact_mask  adhesive mode: N*N bytes, 1 = in contact; read as the starting
+ *                contact area and overwritten with the final one (host or device).
+ *                May be NULL (start from no contact).  Ignored when dgamma == 0. */
+typedef struct {
+  const void* height;
+  const void* p_init;
+  uint8_t* contact_mask;
+  int32_t control;
+  int32_t max_iter;
+  double target;
+  double dgamma;
+  double tol;
+} bem_problem;
+
+/* Scalars of a solve, all in double. */
+typedef struct {
+  double force;       /* delta^2 sum p */
+  double depth;       /* d (given, or found under force control) */
+  double area;        /* delta^2 * number of cells in contact */
+  double a_eq;        /* sqrt(area / pi) */
+  double residual;    /* CG's convergence measure at exit (recursively updated gap) */
+  double err_est;     /* the same measure recomputed from a fresh u = K p */
+  int32_t iters;      /* CG iterations (summed over inner solves in adhesive mode) */
+  int32_t outer_iters;/* adhesive contact-area updates (1 for non-adhesive) */
+  int32_t n_contact;
+  int32_t status;     /* bem_status of this solve */
+  int32_t matvecs;    /* operator products performed */
+  int32_t reserved;
+} bem_result;
+
+/* Builds the operator: evaluates Eq. (9)/(10) in double on the device for every
+ * |k| of the 2N x 2N grid (folded by symmetry to (N+1)^2 values) and stores it in
+ * the kernel's precision.  stream may be NULL (legacy default stream). */
+bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out);
+bem_status bem_destroy_kernel(bem_kernel k);
+
+/* Copies the double-precision compliance table K^(k_ij), i, j in [0, N], row-major
+ * (N+1)*(N+1) doubles, in m/Pa-consistent units (no FFT normalisation), to out
+ * (host or device).  Entry (0,0) is the DC value chosen by dc_mode. */
+bem_status bem_kernel_table(bem_kernel k, void* out, void* cuda_stream);
+
+/* u = K p (Eq. 1 evaluated by Eq. 11).  p and u: N*N, host or device.  Device
+ * arguments: asynchronous on the stream.  Host arguments: returns after u is written. */
+bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream);
+
+/* Solves one contact problem; writes the pressure to p_out (N*N, host or device)
+ * and the scalars to *res (host).  Synchronises the stream before returning.
+ * Non-adhesive: Polonsky-Keer constrained conjugate gradients (the method the
+ * paper cites for the inverse problem, Sec. 2).  Adhesive: Sec. 2's procedure at
+ * one depth: CG on the fixed contact area, penetrating cells join, boundary cells
+ * with tension above sigma_c (Eq. 12, compared in double) detach, repeat. */
+bem_status bem_solve_contact(bem_kernel k, const bem_problem* prob, void* p_out,
+                             bem_result* res, void* cuda_stream);
+
+/* Solves n independent problems (each with its own kernel and grid size).
+ * res is a host array of n results; the return value is BEM_OK if every
+ * instance converged, else the first failing status. */
+bem_status bem_solve_batch(int32_t n, const bem_kernel* kernels, const bem_problem* probs,
+                           void* const* p_out, bem_result* res, void* cuda_stream);
+
+/* Profiling aid (not part of the paper's method): runs `reps` products u = K p
+ * (p, u device arrays) with CUDA events recorded on `cuda_stream` around each of
+ * the three passes, and writes the mean duration of each pass in milliseconds to
+ * ms_out[0] (row forward FFT), ms_out[1] (column FFT x K^ x inverse FFT) and
+ * ms_out[2] (row inverse FFT).  Synchronises the stream. */
+bem_status bem_profile_passes(bem_kernel k, const void* p, void* u, int32_t reps, float* ms_out,
+                              void* cuda_stream);
+
+/* Number of kernel launches the library has issued since it was loaded. */
+int64_t bem_launch_count(void);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* bem_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int32_t bem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H */

@@ -84,3 +84,21 @@ def matvec_fft(Kgrid, p):
     pad[:N, :N] = p
     U = _dft.ifft2(Kgrid * _dft.fft2(pad))
     return U.real[:N, :N].copy()
+
+
+def influence_at(N, delta, h, E1, nu1, E2, nu2, offsets, dc_mode=0):
+    """G at given integer cell offsets (dy, dx) by the direct sum over all M^2 wave
+    numbers, G(x) = (1/M^2) sum_k K(k) cos(k.x) (K is even, so the sine part
+    cancels).  One output at a time: usable at N = 2048."""
+    M = 2 * N
+    Kg = khat_grid(N, delta, h, E1, nu1, E2, nu2, dc_mode)
+    i = np.arange(M)
+    out = []
+    for dy, dx in offsets:
+        cy = np.cos(2.0 * np.pi * i * dy / M)
+        cx = np.cos(2.0 * np.pi * i * dx / M)
+        sy = np.sin(2.0 * np.pi * i * dy / M)
+        sx = np.sin(2.0 * np.pi * i * dx / M)
+        # cos(a + b) = cos a cos b - sin a sin b, summed as two rank-one contractions
+        out.append((cy @ Kg @ cx - sy @ Kg @ sx) / (M * M))
+    return np.array(out)

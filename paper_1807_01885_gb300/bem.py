@@ -1,0 +1,249 @@
+"""ctypes binding of libbem.so (include/bem.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts Python values
+to the C structs, passes tensor/array data pointers and CUDA stream handles, and
+turns status codes into exceptions.  There is no CPU fallback: if the library is
+missing the first call raises.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays, row-major, N x N, of the
+kernel's dtype (float64 for "fp64", float32 for "fp32"); the library detects
+device versus host pointers itself.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbem.so")
+
+BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ENAN, BEM_ECYCLE, BEM_EUNSUPPORTED = range(9)
+STATUS_NAMES = ["BEM_OK", "BEM_EINVAL", "BEM_ENOMEM", "BEM_ECUDA", "BEM_ENOCONV", "BEM_ETIMEOUT", "BEM_ENAN",
+                "BEM_ECYCLE", "BEM_EUNSUPPORTED"]
+BEM_FP64, BEM_FP32 = 0, 1
+BEM_CTRL_DEPTH, BEM_CTRL_FORCE = 0, 1
+BEM_DC_FINITE_PART, BEM_DC_ZERO = 0, 1
+
+# entry points declared in include/bem.h
+EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
+           "bem_solve_batch", "bem_profile_passes", "bem_launch_count", "bem_last_error", "bem_version")
+
+
+class BemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class KernelDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("precision", ctypes.c_int32), ("dc_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("delta", ctypes.c_double), ("h", ctypes.c_double),
+                ("E1", ctypes.c_double), ("nu1", ctypes.c_double), ("E2", ctypes.c_double), ("nu2", ctypes.c_double)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_void_p), ("p_init", ctypes.c_void_p), ("contact_mask", ctypes.c_void_p),
+                ("control", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("target", ctypes.c_double),
+                ("dgamma", ctypes.c_double), ("tol", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("force", ctypes.c_double), ("depth", ctypes.c_double), ("area", ctypes.c_double),
+                ("a_eq", ctypes.c_double), ("residual", ctypes.c_double), ("err_est", ctypes.c_double),
+                ("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32), ("n_contact", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("matvecs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+_lib = None
+
+
+def load(path=None):
+    """Loads libbem.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_1807_01885_gb300.build` "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.bem_make_kernel.argtypes = [ctypes.POINTER(KernelDesc), vp, ctypes.POINTER(vp)]
+    lib.bem_destroy_kernel.argtypes = [vp]
+    lib.bem_kernel_table.argtypes = [vp, vp, vp]
+    lib.bem_matvec.argtypes = [vp, vp, vp, vp]
+    lib.bem_solve_contact.argtypes = [vp, ctypes.POINTER(Problem), vp, ctypes.POINTER(Result), vp]
+    lib.bem_solve_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Problem), ctypes.POINTER(vp),
+                                    ctypes.POINTER(Result), vp]
+    for name in ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
+                 "bem_solve_batch"):
+        getattr(lib, name).restype = i32
+    lib.bem_last_error.restype = ctypes.c_char_p
+    lib.bem_last_error.argtypes = []
+    lib.bem_version.restype = i32
+    lib.bem_version.argtypes = []
+    lib.bem_profile_passes.argtypes = [vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp]
+    lib.bem_profile_passes.restype = i32
+    lib.bem_launch_count.argtypes = []
+    lib.bem_launch_count.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def _check(status, allow=()):
+    if status != BEM_OK and status not in allow:
+        raise BemError(status, load().bem_last_error().decode())
+    return status
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, one to one
+
+def bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART, stream=None):
+    lib = load()
+    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, reserved=0, delta=delta, h=h, E1=E1, nu1=nu1,
+                   E2=E2, nu2=nu2)
+    out = ctypes.c_void_p()
+    _check(lib.bem_make_kernel(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def bem_destroy_kernel(k):
+    _check(load().bem_destroy_kernel(k))
+
+
+def bem_kernel_table(k, out, stream=None):
+    _check(load().bem_kernel_table(k, _ptr(out), _stream(stream)))
+    return out
+
+
+def bem_matvec(k, p, u, stream=None):
+    _check(load().bem_matvec(k, _ptr(p), _ptr(u), _stream(stream)))
+    return u
+
+
+def make_problem(height, control=BEM_CTRL_DEPTH, target=0.0, dgamma=0.0, tol=1e-10, max_iter=10000,
+                 p_init=None, contact_mask=None):
+    return Problem(height=_ptr(height), p_init=_ptr(p_init), contact_mask=_ptr(contact_mask), control=control,
+                   max_iter=max_iter, target=target, dgamma=dgamma, tol=tol)
+
+
+def bem_solve_contact(k, prob, p_out, stream=None, allow=(BEM_ENOCONV,)):
+    res = Result()
+    st = load().bem_solve_contact(k, ctypes.byref(prob), _ptr(p_out), ctypes.byref(res), _stream(stream))
+    _check(st, allow)
+    return res.as_dict()
+
+
+def bem_solve_batch(kernels, probs, p_outs, stream=None):
+    n = len(kernels)
+    karr = (ctypes.c_void_p * n)(*kernels)
+    parr = (Problem * n)(*probs)
+    oarr = (ctypes.c_void_p * n)(*[_ptr(p) for p in p_outs])
+    rarr = (Result * n)()
+    st = load().bem_solve_batch(n, karr, parr, oarr, rarr, _stream(stream))
+    return st, [r.as_dict() for r in rarr]
+
+
+def bem_version():
+    return load().bem_version()
+
+
+def bem_profile_passes(k, p, u, reps, stream=None):
+    ms = (ctypes.c_float * 3)()
+    _check(load().bem_profile_passes(k, _ptr(p), _ptr(u), reps, ms, _stream(stream)))
+    return [ms[0], ms[1], ms[2]]
+
+
+def bem_launch_count():
+    return load().bem_launch_count()
+
+
+# ---------------------------------------------------------------------------
+class Kernel:
+    """Owning wrapper of a bem_kernel handle (same parameters as bem_kernel_desc)."""
+
+    def __init__(self, N, delta, h, E1, nu1, E2, nu2, precision="fp64", dc_mode=BEM_DC_FINITE_PART, stream=None):
+        self.N, self.delta = N, delta
+        self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
+        self.precision = precision
+        prec = BEM_FP64 if precision == "fp64" else BEM_FP32
+        self.handle = bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.precision == "fp64" else np.float32
+
+    def table(self, device="cuda"):
+        import torch
+        out = torch.empty((self.N + 1, self.N + 1), dtype=torch.float64, device=device)
+        return bem_kernel_table(self.handle, out)
+
+    def matvec(self, p, u=None, stream=None):
+        if u is None:
+            import torch
+            u = torch.empty_like(p) if hasattr(p, "data_ptr") else np.empty_like(p)
+        return bem_matvec(self.handle, p, u, stream)
+
+    def solve(self, height, control="depth", target=0.0, dgamma=0.0, tol=1e-10, max_iter=10000, p_init=None,
+              contact_mask=None, p_out=None, stream=None):
+        ctrl = BEM_CTRL_DEPTH if control == "depth" else BEM_CTRL_FORCE
+        if p_out is None:
+            import torch
+            p_out = torch.empty_like(height) if hasattr(height, "data_ptr") else np.empty_like(height)
+        prob = make_problem(height, ctrl, target, dgamma, tol, max_iter, p_init, contact_mask)
+        res = bem_solve_contact(self.handle, prob, p_out, stream)
+        return p_out, res
+
+    def close(self):
+        if getattr(self, "handle", None):
+            bem_destroy_kernel(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+

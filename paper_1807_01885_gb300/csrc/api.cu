@@ -1,0 +1,329 @@
+// C ABI of libbem.so (declared in include/bem.h): argument checks, workspace
+// ownership, host/device argument staging, error reporting.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+bem_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA;
+}
+
+bem_status solve_contact_device(bem_kernel_s* k, const bem_problem* prob, const void* f, const void* pinit,
+                                uint8_t* mask, void* p_out, bem_result* res, cudaStream_t s);
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bem_status check_desc(const bem_kernel_desc* d) {
+  if (d == nullptr) { set_error("desc is NULL"); return BEM_EINVAL; }
+  const int N = d->N;
+  if (N < 4 || N > (1 << MAX_LOGN) || (N & (N - 1))) {
+    set_error("N must be a power of two in [4, 2048]");
+    return BEM_EINVAL;
+  }
+  if (d->precision != BEM_FP64 && d->precision != BEM_FP32) { set_error("unknown precision"); return BEM_EINVAL; }
+  if (d->dc_mode != BEM_DC_FINITE_PART && d->dc_mode != BEM_DC_ZERO) { set_error("unknown dc_mode"); return BEM_EINVAL; }
+  if (!(d->delta > 0.0) || !isfinite(d->delta)) { set_error("delta must be positive and finite"); return BEM_EINVAL; }
+  if (!(d->h >= 0.0) || isnan(d->h)) { set_error("h must be >= 0 (INFINITY allowed)"); return BEM_EINVAL; }
+  if (!(d->E1 > 0.0) || !isfinite(d->E1)) { set_error("E1 must be positive and finite"); return BEM_EINVAL; }
+  if (!(d->E2 > 0.0) || isnan(d->E2)) { set_error("E2 must be positive (INFINITY allowed)"); return BEM_EINVAL; }
+  if (!(d->nu1 >= 0.0 && d->nu1 < 0.5) || !(d->nu2 >= 0.0 && d->nu2 < 0.5)) {
+    set_error("Poisson ratios must lie in [0, 0.5)");
+    return BEM_EINVAL;
+  }
+  return BEM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void free_ws(bem_kernel_s* k) {
+  Workspace& w = k->ws;
+  cudaFree(w.spec);
+  cudaFree(w.table);
+  cudaFree(w.table64);
+  cudaFree(w.tw);
+  cudaFree(w.vec);
+  cudaFree(w.mask);
+  cudaFree(w.partials);
+  cudaFree(w.ticket);
+  cudaFree(w.state);
+  cudaFreeHost(w.state_host);
+  cudaFree(w.stage_in);
+  cudaFree(w.stage_out);
+  w = Workspace{};
+}
+
+// Host <-> device staging of an N*N array argument.
+struct Arg {
+  const void* dev = nullptr;
+  bool host = false;
+};
+
+bem_status stage_in(bem_kernel_s* k, const void* p, void* dst, size_t bytes, cudaStream_t s, Arg* out) {
+  if (p == nullptr) { out->dev = nullptr; return BEM_OK; }
+  if (is_device_ptr(p)) {
+    out->dev = p;
+    out->host = false;
+    return BEM_OK;
+  }
+  BEM_CUDA_TRY(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, s));
+  out->dev = dst;
+  out->host = true;
+  return BEM_OK;
+}
+
+}  // namespace
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" {
+
+int32_t bem_version(void) { return 100; }
+
+int64_t bem_launch_count(void) { return (int64_t)launches(); }
+
+bem_status bem_profile_passes(bem_kernel k, const void* p, void* u, int32_t reps, float* ms_out,
+                              void* cuda_stream) {
+  if (k == nullptr || p == nullptr || u == nullptr || ms_out == nullptr || reps <= 0) {
+    set_error("invalid profiling arguments");
+    return BEM_EINVAL;
+  }
+  if (!is_device_ptr(p) || !is_device_ptr(u)) {
+    set_error("profiling needs device arrays");
+    return BEM_EINVAL;
+  }
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) BEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+  double acc[3] = {0, 0, 0};
+  bem_status st = BEM_OK;
+  for (int r = 0; r < reps && st == BEM_OK; ++r) {
+    cudaEventRecord(ev[0], s);
+    for (int pass = 0; pass < 3; ++pass) {
+      if (k->prec == BEM_FP64)
+        launch_pass<double>(k, pass, (const double*)p, (double*)u, s);
+      else
+        launch_pass<float>(k, pass, (const float*)p, (float*)u, s);
+      cudaEventRecord(ev[pass + 1], s);
+    }
+    cudaError_t e = cudaEventSynchronize(ev[3]);
+    if (e != cudaSuccess) { st = cuda_fail(e, "profile"); break; }
+    for (int pass = 0; pass < 3; ++pass) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[pass], ev[pass + 1]);
+      acc[pass] += ms;
+    }
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  for (int pass = 0; pass < 3; ++pass) ms_out[pass] = (float)(acc[pass] / reps);
+  return st;
+}
+
+const char* bem_last_error(void) { return g_last_error.c_str(); }
+
+bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out) {
+  if (out == nullptr) { set_error("out is NULL"); return BEM_EINVAL; }
+  *out = nullptr;
+  bem_status st = check_desc(desc);
+  if (st != BEM_OK) return st;
+  bem_kernel_s* k = new bem_kernel_s();
+  k->desc = *desc;
+  k->N = desc->N;
+  k->M = 2 * desc->N;
+  k->logN = 0;
+  while ((1 << k->logN) < k->N) ++k->logN;
+  k->prec = desc->precision;
+  k->elem = (k->prec == BEM_FP64) ? sizeof(double) : sizeof(float);
+  cudaGetDevice(&k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)k->N * k->N;
+  Workspace& w = k->ws;
+  auto fail = [&](cudaError_t e, const char* what) {
+    bem_status r = cuda_fail(e, what);
+    free_ws(k);
+    delete k;
+    return r;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&w.spec, spec_bytes(k))) != cudaSuccess) return fail(e, "cudaMalloc(spec)");
+  if ((e = cudaMalloc(&w.table, table_bytes(k))) != cudaSuccess) return fail(e, "cudaMalloc(table)");
+  if ((e = cudaMalloc((void**)&w.table64, (size_t)(k->N + 1) * (k->N + 1) * sizeof(double))) != cudaSuccess)
+    return fail(e, "cudaMalloc(table64)");
+  if ((e = cudaMalloc(&w.tw, (size_t)k->M * 2 * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(tw)");
+  if ((e = cudaMalloc(&w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
+  if ((e = cudaMalloc((void**)&w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
+  if ((e = cudaMalloc((void**)&w.partials, 8 * 1024 * sizeof(double))) != cudaSuccess)
+    return fail(e, "cudaMalloc(partials)");
+  if ((e = cudaMalloc((void**)&w.ticket, sizeof(unsigned int))) != cudaSuccess) return fail(e, "cudaMalloc(ticket)");
+  if ((e = cudaMalloc((void**)&w.state, sizeof(SolveState))) != cudaSuccess) return fail(e, "cudaMalloc(state)");
+  if ((e = cudaMallocHost((void**)&w.state_host, sizeof(SolveState))) != cudaSuccess)
+    return fail(e, "cudaMallocHost(state)");
+  if ((e = cudaMalloc(&w.stage_in, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_in)");
+  if ((e = cudaMalloc(&w.stage_out, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_out)");
+  if ((e = cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(e, "memset(ticket)");
+  st = build_table(k, s);
+  if (st != BEM_OK) {
+    free_ws(k);
+    delete k;
+    return st;
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "build_table");
+  *out = k;
+  return BEM_OK;
+}
+
+bem_status bem_destroy_kernel(bem_kernel k) {
+  if (k == nullptr) return BEM_OK;
+  DeviceGuard g(k->dev);
+  cudaDeviceSynchronize();
+  free_ws(k);
+  delete k;
+  return BEM_OK;
+}
+
+bem_status bem_kernel_table(bem_kernel k, void* out, void* cuda_stream) {
+  if (k == nullptr || out == nullptr) { set_error("NULL argument"); return BEM_EINVAL; }
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = (size_t)(k->N + 1) * (k->N + 1) * sizeof(double);
+  BEM_CUDA_TRY(cudaMemcpyAsync(out, k->ws.table64, bytes, cudaMemcpyDefault, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream) {
+  if (k == nullptr || p == nullptr || u == nullptr) { set_error("NULL argument"); return BEM_EINVAL; }
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = (size_t)k->N * k->N * k->elem;
+  Arg ap;
+  bem_status st = stage_in(k, p, k->ws.stage_in, bytes, s, &ap);
+  if (st != BEM_OK) return st;
+  if (((uintptr_t)ap.dev & 15) != 0) { set_error("p must be 16-byte aligned"); return BEM_EINVAL; }
+  const bool u_host = !is_device_ptr(u);
+  void* ud = u_host ? k->ws.stage_out : u;
+  if (((uintptr_t)ud & 15) != 0) { set_error("u must be 16-byte aligned"); return BEM_EINVAL; }
+  if (k->prec == BEM_FP64)
+    launch_matvec<double>(k, (const double*)ap.dev, (double*)ud, s, nullptr);
+  else
+    launch_matvec<float>(k, (const float*)ap.dev, (float*)ud, s, nullptr);
+  BEM_CUDA_TRY(cudaGetLastError());
+  if (u_host) {
+    BEM_CUDA_TRY(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  } else if (ap.host) {
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));   // the host input must outlive the copy
+  }
+  return BEM_OK;
+}
+
+bem_status bem_solve_contact(bem_kernel k, const bem_problem* prob, void* p_out, bem_result* res,
+                             void* cuda_stream) {
+  if (k == nullptr || prob == nullptr || res == nullptr || prob->height == nullptr) {
+    set_error("NULL argument");
+    return BEM_EINVAL;
+  }
+  if (!(prob->tol > 0.0) || prob->max_iter <= 0 || !(prob->dgamma >= 0.0) || !isfinite(prob->target)) {
+    set_error("invalid problem (tol > 0, max_iter > 0, dgamma >= 0, finite target)");
+    return BEM_EINVAL;
+  }
+  if (prob->control != BEM_CTRL_DEPTH && prob->control != BEM_CTRL_FORCE) {
+    set_error("unknown control");
+    return BEM_EINVAL;
+  }
+  if (prob->control == BEM_CTRL_FORCE && (prob->dgamma > 0.0 || !(prob->target > 0.0))) {
+    set_error("force control needs dgamma == 0 and a positive force");
+    return BEM_EINVAL;
+  }
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)k->N * k->N;
+  const size_t bytes = n * k->elem;
+  char* vec = (char*)k->ws.vec;
+  // the height map goes straight into the solver's f slot; the warm start into x
+  void* fslot = vec + 5 * bytes;
+  void* xslot = vec + 6 * bytes;
+  const bool f_dev = is_device_ptr(prob->height);
+  BEM_CUDA_TRY(cudaMemcpyAsync(fslot, prob->height, bytes, f_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  const void* pinit = nullptr;
+  if (prob->p_init != nullptr) {
+    const bool d = is_device_ptr(prob->p_init);
+    BEM_CUDA_TRY(cudaMemcpyAsync(xslot, prob->p_init, bytes, d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    pinit = xslot;
+  }
+  uint8_t* mask = k->ws.mask;
+  bool mask_dev = false;
+  if (prob->dgamma > 0.0) {
+    if (prob->contact_mask != nullptr) {
+      mask_dev = is_device_ptr(prob->contact_mask);
+      BEM_CUDA_TRY(cudaMemcpyAsync(mask, prob->contact_mask, n,
+                                   mask_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    } else {
+      BEM_CUDA_TRY(cudaMemsetAsync(mask, 0, n, s));
+    }
+  }
+  const bool out_host = (p_out != nullptr) && !is_device_ptr(p_out);
+  void* pout_dev = out_host ? k->ws.stage_out : p_out;
+  bem_status st = solve_contact_device(k, prob, fslot, pinit, mask, pout_dev, res, s);
+  if (st == BEM_ECUDA || st == BEM_ENOMEM || st == BEM_EINVAL) return st;
+  if (out_host) BEM_CUDA_TRY(cudaMemcpyAsync(p_out, pout_dev, bytes, cudaMemcpyDeviceToHost, s));
+  if (prob->dgamma > 0.0 && prob->contact_mask != nullptr)
+    BEM_CUDA_TRY(cudaMemcpyAsync(prob->contact_mask, mask, n, mask_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+}
+
+bem_status bem_solve_batch(int32_t n, const bem_kernel* kernels, const bem_problem* probs, void* const* p_out,
+                           bem_result* res, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (kernels == nullptr || probs == nullptr || res == nullptr))) {
+    set_error("invalid batch arguments");
+    return BEM_EINVAL;
+  }
+  bem_status first = BEM_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    bem_status st = bem_solve_contact(kernels[i], &probs[i], p_out ? p_out[i] : nullptr, &res[i], cuda_stream);
+    if (st != BEM_OK) {
+      res[i].status = st;
+      if (first == BEM_OK) first = st;
+    }
+  }
+  return first;
+}
+
+}  // extern "C"

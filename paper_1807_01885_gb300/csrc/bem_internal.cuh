@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libbem.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "bem.h"
+
+namespace bem {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+__host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+__host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return mk(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return mk(a.y, -a.x); }
+template <typename C> __device__ __forceinline__ C cmul_pi(C a) { return mk(-a.y, a.x); }
+
+// ---------------------------------------------------------------------------
+// Layout constants.
+// Spectrum (after the row pass) is stored column-block-major: for column block
+// cb (TC consecutive frequencies), an N x TC row-major sub-array:
+//     spec[((cb * N) + r) * TC + tc],  j = cb * TC + tc,  cb in [0, N/TC].
+// The last block holds only the Nyquist column j = N at tc = 0.
+constexpr int TC = 4;
+constexpr int NTHREADS = 256;
+constexpr int MAX_LOGN = 11;   // N <= 2048
+
+// Device-side scalar state of a solve (double throughout).
+struct SolveState {
+  double d;          // current depth
+  double gbar;       // mean gap over the contact set (force control)
+  double G, Gold;    // sum of squared gaps, previous value
+  double beta;       // CG direction factor
+  double flag;       // 1 = conjugate step allowed, 0 = steepest descent restart
+  double tau;        // step length
+  double rbar;       // mean of K t over the contact set (force control)
+  double res;        // relative residual
+  double sum_p;      // sum of pressures after the update
+  double scale;      // pending load-control rescale of p (1 = none)
+  double target;     // F under force control
+  double delta2;     // delta^2
+  double tol;
+  double rr, rr_new, b2;       // linear CG (adhesive inner solve)
+  double alpha;
+  double sig_c;      // Eq. (12) detachment stress
+  uint64_t mask_hash;
+  int n_c;           // contact cells at the start of the iteration
+  int n_neg, n_ol;   // projected cells, re-activated cells
+  int n_add, n_detach;
+  int iter;
+  int done;          // 1 once converged
+  int refresh;       // 1: recompute u = K p before the next step
+  int status;        // bem_status raised on the device (BEM_ENAN)
+  int control;
+  int max_iter;
+  int matvecs;
+  int mv_p_on;       // gate of the refresh product u = K p (1 = run)
+  int mv_t_on;       // gate of the search-direction product (1 = run, i.e. not done)
+  int pad_;
+};
+
+// Workspace owned by a kernel handle.
+struct Workspace {
+  void* spec = nullptr;      // (N/TC + 1) * N * TC complex
+  void* table = nullptr;     // (N/TC + 1) * (N+1) * TC real, blocked, scaled by 1/M^2
+  double* table64 = nullptr; // (N+1)^2 doubles, unscaled, row-major
+  void* tw = nullptr;        // M complex: e^{-2 pi i k / M}
+  void* vec = nullptr;       // solver vectors: p, g, t, r, u, f, x (N*N each)
+  uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy
+  double* partials = nullptr;// per-block partial sums
+  unsigned int* ticket = nullptr;
+  SolveState* state = nullptr;
+  SolveState* state_host = nullptr;   // pinned mirror
+  void* stage_in = nullptr;  // staging for host arguments (N*N)
+  void* stage_out = nullptr;
+};
+
+}  // namespace bem
+
+struct bem_kernel_s {
+  bem_kernel_desc desc;
+  int N, M, logN;
+  int prec;       // BEM_FP64 / BEM_FP32
+  size_t elem;    // sizeof(real)
+  int dev;
+  bem::Workspace ws;
+};
+
+namespace bem {
+void set_error(const std::string& msg);
+// number of kernel launches issued by the library (for launch accounting)
+void note_launches(long long n);
+long long launches();
+bem_status cuda_fail(cudaError_t e, const char* what);
+
+// matvec.cu
+bem_status build_table(bem_kernel_s* k, cudaStream_t s);
+template <typename T>
+void launch_matvec(const bem_kernel_s* k, const T* p, T* u, cudaStream_t s, const int* skip_flag);
+// one pass of the product (0 = rows forward, 1 = columns, 2 = rows inverse)
+template <typename T>
+void launch_pass(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStream_t s);
+size_t spec_bytes(const bem_kernel_s* k);
+size_t table_bytes(const bem_kernel_s* k);
+
+// solve.cu
+bem_status solve_contact(bem_kernel_s* k, const bem_problem* prob, void* p_out, bem_result* res,
+                         cudaStream_t s);
+}  // namespace bem
+
+#define BEM_CUDA_TRY(call)                                     \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return bem::cuda_fail(e_, #call);   \
+  } while (0)

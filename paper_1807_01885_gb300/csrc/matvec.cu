@@ -1,0 +1,313 @@
+// The surface operator u = K p (Eq. 1) evaluated as in Eq. (11) on a 2N x 2N period.
+//
+// Three passes, all zero-padding aware (the padded half is never stored):
+//  1. row pass    : per row r < N, the length-2N real FFT of (p[r, 0..N-1], 0...),
+//                   kept for frequencies j in [0, N] (Hermitian half).  The real row
+//                   is packed as N/2 complex values z[m] = p[2m] + i p[2m+1]; the
+//                   length-N complex FFT of the half-zero sequence z splits into two
+//                   length-N/2 FFTs (even and odd outputs); the standard real-FFT
+//                   recombination then gives X[j].
+//  2. column pass : per frequency column j, the length-2N FFT of the N nonzero rows
+//                   splits into FFT_N(y) (even wave numbers) and FFT_N(y e^{-2 pi i r/2N})
+//                   (odd ones); each is multiplied by the compliance K^(|k|) of Eq. (9)
+//                   (table scaled by 1/(2N)^2), inverse-transformed, and the two
+//                   halves recombine into the first N rows of the inverse transform.
+//  3. row inverse : the inverse real FFT of each row, evaluated only at the first N
+//                   outputs (the window), via the same packing in reverse.
+#include <math.h>
+
+#include "bem_internal.cuh"
+#include "fft.cuh"
+
+namespace bem {
+
+// ---------------------------------------------------------------------------
+// Compliance table (Eqs. 9, 10), evaluated in double on the device.
+struct KernelParams {
+  double c_pref;   // 2 (1 - nu1^2) / E1
+  double A, B, C, D;
+  double h;
+  double kstep;    // 2 pi / (M delta)
+  double dc;       // value at k = 0
+  int N;
+  int homog;       // h = inf: Eq. (4) with E1, nu1
+};
+
+__global__ void k_table64(double* __restrict__ t64, KernelParams P) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j > P.N) return;
+  double val;
+  if (i == 0 && j == 0) {
+    val = P.dc;
+  } else {
+    const double k = P.kstep * sqrt((double)(i * i + j * j));
+    if (P.homog) {
+      val = P.c_pref / k;
+    } else {
+      const double x = k * P.h;
+      const double e2 = exp(-2.0 * x);
+      const double e4 = e2 * e2;
+      const double num = P.A * e4 + P.B * x * e2 + P.D;
+      const double den = -P.A * e4 - P.B * x * x * e2 + 2.0 * P.C * e2 + P.D;
+      val = P.c_pref * num / (k * den);
+    }
+  }
+  t64[(size_t)i * (P.N + 1) + j] = val;
+}
+
+// Blocked copy in the path precision, scaled by 1/M^2:
+// table[(cb (N+1) + i) TC + tc] = K(i, cb TC + tc) / M^2 (0 past j = N).
+template <typename T>
+__global__ void k_table_block(const double* __restrict__ t64, T* __restrict__ tab, int N, double scale) {
+  const int nblk = N / TC + 1;
+  const size_t total = (size_t)nblk * (N + 1) * TC;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int tc = (int)(idx % TC);
+    const size_t rest = idx / TC;
+    const int i = (int)(rest % (N + 1));
+    const int cb = (int)(rest / (N + 1));
+    const int j = cb * TC + tc;
+    tab[idx] = (j <= N) ? (T)(t64[(size_t)i * (N + 1) + j] * scale) : (T)0;
+  }
+}
+
+template <typename T>
+__global__ void k_twiddles(cplx<T>* __restrict__ tw, int M) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)M, &s, &c);
+    tw[m] = mk((T)c, (T)(-s));
+  }
+}
+
+// Normalised constants of Eq. (10): every constant is a quadratic form in
+// a = E2 (1 + nu1), b = E1 (1 + nu2); dividing all four by (a + b)^2 leaves
+// the ratio of Eq. (9) unchanged and stays finite for E2 = inf.
+static void layered_constants(const bem_kernel_desc& d, double* A, double* B, double* C, double* D) {
+  double al, be;
+  if (isinf(d.E2)) {
+    al = 1.0;
+    be = 0.0;
+  } else {
+    const double a = d.E2 * (1.0 + d.nu1), b = d.E1 * (1.0 + d.nu2);
+    al = a / (a + b);
+    be = b / (a + b);
+  }
+  const double n1 = d.nu1, n2 = d.nu2;
+  *A = ((3.0 - 4.0 * n1) * al - (3.0 - 4.0 * n2) * be) * (be - al);
+  *B = 4.0 * (al + (3.0 - 4.0 * n2) * be) * (be - al);
+  *C = (4.0 * n2 - 3.0) * be * be - 2.0 * (2.0 * n1 - 1.0) * (2.0 * n2 - 1.0) * al * be +
+       (8.0 * n1 * n1 - 12.0 * n1 + 5.0) * al * al;
+  *D = (al + (3.0 - 4.0 * n2) * be) * ((3.0 - 4.0 * n1) * al + be);
+}
+
+size_t spec_bytes(const bem_kernel_s* k) {
+  return (size_t)(k->N / TC + 1) * k->N * TC * 2 * k->elem;
+}
+size_t table_bytes(const bem_kernel_s* k) {
+  return (size_t)(k->N / TC + 1) * (k->N + 1) * TC * k->elem;
+}
+
+bem_status build_table(bem_kernel_s* k, cudaStream_t s) {
+  const bem_kernel_desc& d = k->desc;
+  KernelParams P;
+  P.N = k->N;
+  P.c_pref = 2.0 * (1.0 - d.nu1 * d.nu1) / d.E1;
+  P.h = d.h;
+  P.kstep = 2.0 * M_PI / ((double)k->M * d.delta);
+  P.homog = isinf(d.h) ? 1 : 0;
+  layered_constants(d, &P.A, &P.B, &P.C, &P.D);
+  // DC finite part: k K(k) = c F(kh), F = num/den; lim [K - F(0) c / k] = c h F'(0)
+  // with num'(0) = B - 4A and den'(0) = 4A - 4C.
+  if (P.homog || d.dc_mode == BEM_DC_ZERO) {
+    P.dc = 0.0;
+  } else {
+    const double n0 = P.A + P.D, d0 = -P.A + 2.0 * P.C + P.D;
+    const double dn = P.B - 4.0 * P.A, dd = 4.0 * P.A - 4.0 * P.C;
+    P.dc = P.c_pref * d.h * (dn * d0 - n0 * dd) / (d0 * d0);
+  }
+  dim3 grid((k->N + 1 + 127) / 128, k->N + 1);
+  k_table64<<<grid, 128, 0, s>>>(k->ws.table64, P);
+  note_launches(3);
+  BEM_CUDA_TRY(cudaGetLastError());
+  const double scale = 1.0 / ((double)k->M * (double)k->M);
+  if (k->prec == BEM_FP64) {
+    k_table_block<double><<<256, 256, 0, s>>>(k->ws.table64, (double*)k->ws.table, k->N, scale);
+    k_twiddles<double><<<(k->M + 255) / 256, 256, 0, s>>>((double2*)k->ws.tw, k->M);
+  } else {
+    k_table_block<float><<<256, 256, 0, s>>>(k->ws.table64, (float*)k->ws.table, k->N, scale);
+    k_twiddles<float><<<(k->M + 255) / 256, 256, 0, s>>>((float2*)k->ws.tw, k->M);
+  }
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: rows, real -> half spectrum.  Block = TR rows.
+template <typename T, int TR>
+__global__ void __launch_bounds__(NTHREADS)
+k_row_fwd(const T* __restrict__ p, cplx<T>* __restrict__ spec, const cplx<T>* __restrict__ tw, int logN,
+          const int* __restrict__ skip) {
+  using C = cplx<T>;
+  if (skip != nullptr && *skip == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN, logH = logN - 1, H = N >> 1;
+  C* a = reinterpret_cast<C*>(smem_raw);
+  C* b = a + TR * N;
+  const int r0 = blockIdx.x * TR;
+  // sequences (rl, 0): z[m];  (rl, 1): z[m] e^{-2 pi i m/N}   (m < N/2)
+  for (int idx = threadIdx.x; idx < TR * H; idx += blockDim.x) {
+    const int rl = idx >> logH, m = idx & (H - 1);
+    const C z = reinterpret_cast<const C*>(p + (size_t)(r0 + rl) * N)[m];
+    a[(2 * rl) * H + m] = z;
+    a[(2 * rl + 1) * H + m] = cmul(z, tw[2 * m]);
+  }
+  __syncthreads();
+  const C* Z = block_fft<false>(a, b, logH, 2 * TR, tw, logN + 1);
+  // X[j] = (Z[j] + Z*[N-j])/2 + e^{-2 pi i j/M} (Z[j] - Z*[N-j])/(2i),  j in [0, N]
+  const int nblk = N / TC + 1;
+  for (int idx = threadIdx.x; idx < nblk * TR * TC; idx += blockDim.x) {
+    const int cb = idx / (TR * TC);
+    const int q = idx - cb * (TR * TC);
+    const int rl = q / TC, tc = q - rl * TC;
+    const int j = cb * TC + tc;
+    C X = mk((T)0, (T)0);
+    if (j <= N) {
+      const int j1 = j & (N - 1), j2 = (N - j) & (N - 1);
+      const C za = Z[(2 * rl + (j1 & 1)) * H + (j1 >> 1)];
+      const C zb = cconj(Z[(2 * rl + (j2 & 1)) * H + (j2 >> 1)]);
+      const C E = cscale(cadd(za, zb), (T)0.5);
+      const C O = cscale(cmul_mi(csub(za, zb)), (T)0.5);
+      X = cadd(E, cmul(O, tw[j]));
+    }
+    spec[((size_t)cb * N + r0) * TC + q] = X;
+  }
+}
+
+// Pass 2: columns, FFT -> x K^ -> IFFT, cropped to N rows.  Block = one column block.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_col(cplx<T>* __restrict__ spec, const T* __restrict__ table, const cplx<T>* __restrict__ tw, int logN,
+      const int* __restrict__ skip) {
+  using C = cplx<T>;
+  if (skip != nullptr && *skip == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN, M = 2 * N;
+  C* a = reinterpret_cast<C*>(smem_raw);
+  C* b = a + 2 * N;
+  const int cb = blockIdx.x;
+  const int ncols = (cb == N / TC) ? 1 : TC;
+  for (int tc = 0; tc < ncols; ++tc) {
+    C* col = spec + (size_t)cb * N * TC + tc;
+    const T* kt = table + (size_t)cb * (N + 1) * TC + tc;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const C y = col[(size_t)r * TC];
+      a[r] = y;
+      a[N + r] = cmul(y, tw[r]);
+    }
+    __syncthreads();
+    C* V = block_fft<false>(a, b, logN, 2, tw, logN + 1);
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      const int ie = 2 * q, io = 2 * q + 1;
+      const int fe = min(ie, M - ie), fo = min(io, M - io);
+      V[q] = cscale(V[q], kt[(size_t)fe * TC]);
+      V[N + q] = cscale(V[N + q], kt[(size_t)fo * TC]);
+    }
+    __syncthreads();
+    C* W = block_fft<true>(V, (V == a) ? b : a, logN, 2, tw, logN + 1);
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      col[(size_t)r * TC] = cadd(W[r], cmulc(W[N + r], tw[r]));
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 3: rows, half spectrum -> real, first N outputs.  Block = TR rows.
+template <typename T, int TR>
+__global__ void __launch_bounds__(NTHREADS)
+k_row_inv(const cplx<T>* __restrict__ spec, T* __restrict__ u, const cplx<T>* __restrict__ tw, int logN,
+          const int* __restrict__ skip) {
+  using C = cplx<T>;
+  if (skip != nullptr && *skip == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN, logH = logN - 1, H = N >> 1;
+  C* a = reinterpret_cast<C*>(smem_raw);
+  C* b = a + TR * N;
+  const int r0 = blockIdx.x * TR;
+  // Zi[j] = (Y[j] + Y*[N-j]) + i (Y[j] - Y*[N-j]) e^{+2 pi i j/M},  j in [0, N)
+  for (int idx = threadIdx.x; idx < (N / TC) * TR * TC; idx += blockDim.x) {
+    const int cb = idx / (TR * TC);
+    const int q = idx - cb * (TR * TC);
+    const int rl = q / TC, tc = q - rl * TC;
+    const int j = cb * TC + tc;
+    const int jr = N - j;
+    const C y1 = spec[((size_t)cb * N + r0) * TC + q];
+    const C y2 = cconj(spec[((size_t)(jr / TC) * N + r0 + rl) * TC + (jr % TC)]);
+    const C e = cadd(y1, y2);
+    const C o = cmul_pi(cmulc(csub(y1, y2), tw[j]));
+    a[(2 * rl + (j & 1)) * H + (j >> 1)] = cadd(e, o);
+  }
+  __syncthreads();
+  const C* z = block_fft<true>(a, b, logH, 2 * TR, tw, logN + 1);
+  // z[m] = Ze[m] + e^{+2 pi i m/N} Zo[m];  u[r, 2m] = Re z, u[r, 2m+1] = Im z
+  for (int idx = threadIdx.x; idx < TR * H; idx += blockDim.x) {
+    const int rl = idx >> logH, m = idx & (H - 1);
+    const C v = cadd(z[(2 * rl) * H + m], cmulc(z[(2 * rl + 1) * H + m], tw[2 * m]));
+    reinterpret_cast<C*>(u + (size_t)(r0 + rl) * N)[m] = v;
+  }
+}
+
+template <typename T> struct RowsPerBlock;
+template <> struct RowsPerBlock<float> { static constexpr int value = 4; };
+template <> struct RowsPerBlock<double> { static constexpr int value = 2; };
+
+template <typename T>
+static void set_smem_attrs() {
+  using C = cplx<T>;
+  constexpr int TR = RowsPerBlock<T>::value;
+  static bool done = false;
+  if (done) return;
+  const int max_row = 2 * TR * (1 << MAX_LOGN) * (int)sizeof(C);
+  const int max_col = 4 * (1 << MAX_LOGN) * (int)sizeof(C);
+  cudaFuncSetAttribute(k_row_fwd<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_row);
+  cudaFuncSetAttribute(k_row_inv<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_row);
+  cudaFuncSetAttribute(k_col<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_col);
+  done = true;
+}
+
+template <typename T>
+static void pass_impl(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStream_t s, const int* skip) {
+  using C = cplx<T>;
+  constexpr int TR = RowsPerBlock<T>::value;
+  set_smem_attrs<T>();
+  const int N = k->N, logN = k->logN;
+  const size_t smem_row = (size_t)2 * TR * N * sizeof(C);
+  const size_t smem_col = (size_t)4 * N * sizeof(C);
+  C* spec = (C*)k->ws.spec;
+  const C* tw = (const C*)k->ws.tw;
+  if (pass == 0) k_row_fwd<T, TR><<<N / TR, NTHREADS, smem_row, s>>>(p, spec, tw, logN, skip);
+  if (pass == 1) k_col<T><<<N / TC + 1, NTHREADS, smem_col, s>>>(spec, (const T*)k->ws.table, tw, logN, skip);
+  if (pass == 2) k_row_inv<T, TR><<<N / TR, NTHREADS, smem_row, s>>>(spec, u, tw, logN, skip);
+  note_launches(1);
+}
+
+template <typename T>
+void launch_matvec(const bem_kernel_s* k, const T* p, T* u, cudaStream_t s, const int* skip) {
+  pass_impl<T>(k, 0, p, u, s, skip);
+  pass_impl<T>(k, 1, p, u, s, skip);
+  pass_impl<T>(k, 2, p, u, s, skip);
+}
+
+template <typename T>
+void launch_pass(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStream_t s) {
+  pass_impl<T>(k, pass, p, u, s, nullptr);
+}
+
+template void launch_pass<float>(const bem_kernel_s*, int, const float*, float*, cudaStream_t);
+template void launch_pass<double>(const bem_kernel_s*, int, const double*, double*, cudaStream_t);
+template void launch_matvec<float>(const bem_kernel_s*, const float*, float*, cudaStream_t, const int*);
+template void launch_matvec<double>(const bem_kernel_s*, const double*, double*, cudaStream_t, const int*);
+
+}  // namespace bem

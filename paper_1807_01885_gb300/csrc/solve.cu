@@ -1,0 +1,761 @@
+// Contact solves (Sec. 2): the inverse problem by Polonsky-Keer constrained
+// conjugate gradients (non-adhesive, depth or force control) and the adhesive
+// displacement-controlled procedure with the detachment criterion of Eq. (12).
+//
+// Every step runs on the device.  Scalars live in a device SolveState; reducing
+// kernels finish their sums in the last block (reduce.cuh) and update the state
+// there, so the host only launches work and reads the state once per chunk of
+// iterations.  Every kernel returns at once when state.done is set.
+//
+// Gap tracking: the gap g = u + f - d is updated recursively (g -= tau K t) while
+// the contact set is unchanged, which is exact in exact arithmetic and keeps the
+// residual free of the cancellation in u + f - d; whenever a cell enters or leaves
+// the set, u = K p is recomputed before the next step.
+#include <math.h>
+
+#include <algorithm>
+#include <unordered_set>
+#include <vector>
+
+#include "bem_internal.cuh"
+#include "reduce.cuh"
+
+namespace bem {
+
+namespace {
+
+constexpr int CHUNK = 8;   // iterations launched between host checks
+
+template <typename T>
+struct DV {
+  T *p, *g, *t, *r, *u, *f, *x;
+};
+
+template <typename T>
+DV<T> dv(const bem_kernel_s* k) {
+  const size_t n = (size_t)k->N * k->N;
+  T* base = (T*)k->ws.vec;
+  return DV<T>{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
+}
+
+int red_blocks(size_t n) {
+  size_t b = (n + NTHREADS * 8 - 1) / (NTHREADS * 8);
+  b = std::max<size_t>(1, std::min<size_t>(b, RED_MAX_BLOCKS));
+  return (int)b;
+}
+
+#define GRID_STRIDE(i, n) \
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void finish(SolveState* st, int status) {
+  st->done = 1;
+  st->mv_p_on = 0;
+  st->mv_t_on = 0;
+  if (status != BEM_OK && st->status == BEM_OK) st->status = status;
+}
+
+// ---------------------------------------------------------------------------
+// Polonsky-Keer CG kernels
+
+// Initial guess for depth control: q = max(d - f, 0) scaled by the energy-optimal
+// factor s = <q, d - f> / <q, K q>; the gap then follows from u = K q as s u + f - d.
+template <typename T>
+__global__ void k_init_q(const T* __restrict__ f, T* __restrict__ q, double d, size_t n) {
+  GRID_STRIDE(i, n) q[i] = (T)fmax((double)d - (double)f[i], 0.0);
+}
+
+template <typename T>
+__global__ void k_init_scale(const T* __restrict__ f, const T* __restrict__ q, const T* __restrict__ u,
+                             double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  Acc<T> a0, a1;
+  const T d = (T)st->d;
+  GRID_STRIDE(i, n) {
+    const T qi = q[i];
+    a0.add(qi * (d - f[i]));
+    a1.add(qi * u[i]);
+  }
+  double v[2] = {a0.value(), a1.value()}, tot[2];
+  if (grid_reduce<2>(v, partials, ticket, tot)) {
+    st->scale = (tot[1] > 0.0) ? tot[0] / tot[1] : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void k_init_apply(const T* __restrict__ f, const T* __restrict__ q, const T* __restrict__ u,
+                             T* __restrict__ p, T* __restrict__ g, const SolveState* st, size_t n) {
+  const T s = (T)st->scale;
+  const double d = st->d;
+  GRID_STRIDE(i, n) {
+    p[i] = s * q[i];
+    g[i] = s * u[i] + (T)((double)f[i] - d);
+  }
+}
+
+// Refresh of the gap after the contact set changed: g = s u + f - d, p *= s, where
+// u = K p was computed from the pressure before the pending load rescale s.
+template <typename T>
+__global__ void k_gap(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ p, T* __restrict__ g,
+                      const SolveState* st, size_t n) {
+  if (st->done || !st->refresh) return;
+  const T s = (T)st->scale;
+  const double d = st->d;
+  GRID_STRIDE(i, n) {
+    g[i] = s * u[i] + (T)((double)f[i] - d);
+    p[i] = s * p[i];
+  }
+}
+
+// Start of an iteration: apply a pending load rescale (if no refresh did), then
+// sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2.
+template <typename T>
+__global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, double* partials,
+                           unsigned int* ticket, SolveState* st, size_t n) {
+  if (st->done) return;
+  const double s = st->scale, d = st->d;
+  const bool apply = (!st->refresh) && (s != 1.0);
+  const T sT = (T)s, s1 = (T)(s - 1.0);
+  Acc<T> ag, agg, auu;
+  double cnt = 0.0;
+  GRID_STRIDE(i, n) {
+    T pi = p[i], gi = g[i];
+    const T fi = f[i];
+    if (apply) {
+      pi = sT * pi;
+      gi = sT * gi + s1 * (T)(d - (double)fi);
+      p[i] = pi;
+      g[i] = gi;
+    }
+    if (pi > (T)0) {
+      const T ui = gi - (T)((double)fi - d);
+      ag.add(gi);
+      agg.add(gi * gi);
+      auu.add(ui * ui);
+      cnt += 1.0;
+    }
+  }
+  double v[4] = {ag.value(), cnt, agg.value(), auu.value()}, tot[4];
+  if (grid_reduce<4>(v, partials, ticket, tot)) {
+    st->scale = 1.0;
+    st->refresh = 0;
+    st->n_c = (int)tot[1];
+    if (st->n_c == 0) {
+      finish(st, st->control == BEM_CTRL_FORCE ? BEM_ENOCONV : BEM_OK);
+      st->res = 0.0;
+      return;
+    }
+    const double gbar = (st->control == BEM_CTRL_FORCE) ? tot[0] / tot[1] : 0.0;
+    const double G = (st->control == BEM_CTRL_FORCE) ? fmax(tot[2] - tot[1] * gbar * gbar, 0.0) : tot[2];
+    st->gbar = gbar;
+    st->G = G;
+    st->res = (tot[3] > 0.0) ? sqrt(G / tot[3]) : 0.0;
+    if (!isfinite(G) || !isfinite(st->res)) {
+      finish(st, BEM_ENAN);
+      return;
+    }
+    if (st->res <= st->tol && st->n_neg == 0 && st->n_ol == 0) {
+      finish(st, BEM_OK);
+      return;
+    }
+    if (st->iter >= st->max_iter) {
+      finish(st, BEM_ENOCONV);
+      return;
+    }
+    st->beta = st->flag * G / st->Gold;
+    st->Gold = G;
+    st->d += gbar;
+  }
+}
+
+// Search direction: g -= gbar (force control), t = g + beta t on Ic, 0 elsewhere.
+template <typename T>
+__global__ void k_pk_dir(const T* __restrict__ p, T* __restrict__ g, T* __restrict__ t, const SolveState* st,
+                         size_t n) {
+  if (st->done) return;
+  const T gbar = (T)st->gbar, beta = (T)st->beta;
+  const bool shift = st->gbar != 0.0;
+  GRID_STRIDE(i, n) {
+    T gi = g[i];
+    if (shift) {
+      gi -= gbar;
+      g[i] = gi;
+    }
+    t[i] = (p[i] > (T)0) ? gi + beta * t[i] : (T)0;
+  }
+}
+
+// Step length: tau = <g, t>_Ic / <r - rbar, t>_Ic with r = K t.
+template <typename T>
+__global__ void k_pk_rt(const T* __restrict__ p, const T* __restrict__ g, const T* __restrict__ t,
+                        const T* __restrict__ r, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  if (st->done) return;
+  Acc<T> art, ar, at, agt;
+  GRID_STRIDE(i, n) {
+    if (p[i] > (T)0) {
+      const T ti = t[i], ri = r[i];
+      art.add(ri * ti);
+      ar.add(ri);
+      at.add(ti);
+      agt.add(g[i] * ti);
+    }
+  }
+  double v[4] = {art.value(), ar.value(), at.value(), agt.value()}, tot[4];
+  if (grid_reduce<4>(v, partials, ticket, tot)) {
+    const double rbar = (st->control == BEM_CTRL_FORCE) ? tot[1] / (double)st->n_c : 0.0;
+    const double den = tot[0] - rbar * tot[2];
+    const double tau = tot[3] / den;
+    if (!(den > 0.0) || !isfinite(tau)) {
+      finish(st, BEM_ENAN);
+      return;
+    }
+    st->rbar = rbar;
+    st->tau = tau;
+  }
+}
+
+// Update: p -= tau t on Ic with projection to p >= 0; cells outside Ic with a
+// negative gap re-enter with p = -tau g; g -= tau K t.
+template <typename T>
+__global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
+                            double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  if (st->done) return;
+  const T tau = (T)st->tau;
+  Acc<T> asum;
+  double nneg = 0.0, nol = 0.0;
+  GRID_STRIDE(i, n) {
+    const T pi = p[i], gi = g[i];
+    T pn;
+    if (pi > (T)0) {
+      pn = pi - tau * t[i];
+      if (pn < (T)0) {
+        pn = (T)0;
+        nneg += 1.0;
+      }
+    } else if (gi < (T)0) {
+      pn = -tau * gi;
+      nol += 1.0;
+    } else {
+      pn = (T)0;
+    }
+    p[i] = pn;
+    g[i] = gi - tau * r[i];
+    asum.add(pn);
+  }
+  double v[3] = {asum.value(), nneg, nol}, tot[3];
+  if (grid_reduce<3>(v, partials, ticket, tot)) {
+    st->sum_p = tot[0];
+    st->n_neg = (int)tot[1];
+    st->n_ol = (int)tot[2];
+    st->flag = (st->n_ol > 0) ? 0.0 : 1.0;
+    st->refresh = (st->n_neg + st->n_ol > 0) ? 1 : 0;
+    st->mv_p_on = st->refresh;
+    st->iter += 1;
+    st->matvecs += 1 + (st->refresh ? 1 : 0);
+    if (st->control == BEM_CTRL_FORCE) {
+      if (!(tot[0] > 0.0)) {
+        finish(st, BEM_ENOCONV);
+        return;
+      }
+      st->scale = st->target / (st->delta2 * tot[0]);
+    }
+  }
+}
+
+// Final statistics from a fresh u = K p: sums over {p > 0} of g, g^2, u^2, count,
+// and sum p over all cells.
+template <typename T>
+__global__ void k_final_stats(const T* __restrict__ p, const T* __restrict__ u, const T* __restrict__ f,
+                              double* partials, unsigned int* ticket, double d, double* out, size_t n) {
+  Acc<T> ag, agg, auu, ap;
+  double cnt = 0.0;
+  GRID_STRIDE(i, n) {
+    const T pi = p[i];
+    ap.add(pi);
+    if (pi != (T)0) {
+      const T ui = u[i];
+      const T gi = ui + (T)((double)f[i] - d);
+      ag.add(gi);
+      agg.add(gi * gi);
+      auu.add(ui * ui);
+      cnt += 1.0;
+    }
+  }
+  double v[5] = {ag.value(), agg.value(), auu.value(), cnt, ap.value()}, tot[5];
+  if (grid_reduce<5>(v, partials, ticket, tot)) {
+    for (int s = 0; s < 5; ++s) out[s] = tot[s];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adhesive procedure kernels (fixed contact area C, p free in sign)
+
+template <typename T>
+__global__ void k_mask_restrict(T* __restrict__ x, const uint8_t* __restrict__ C, size_t n) {
+  GRID_STRIDE(i, n) if (!C[i]) x[i] = (T)0;
+}
+
+// r = (d - f - K x) on C, s = r; sums |r|^2 and |d - f|^2 over C.
+template <typename T>
+__global__ void k_lin_init(const T* __restrict__ u, const T* __restrict__ f, const uint8_t* __restrict__ C,
+                           T* __restrict__ r, T* __restrict__ s, double* partials, unsigned int* ticket,
+                           SolveState* st, size_t n) {
+  const double d = st->d;
+  Acc<T> arr, abb;
+  GRID_STRIDE(i, n) {
+    T ri = (T)0;
+    if (C[i]) {
+      const T bi = (T)(d - (double)f[i]);
+      ri = bi - u[i];
+      arr.add(ri * ri);
+      abb.add(bi * bi);
+    }
+    r[i] = ri;
+    s[i] = ri;
+  }
+  double v[2] = {arr.value(), abb.value()}, tot[2];
+  if (grid_reduce<2>(v, partials, ticket, tot)) {
+    st->rr = tot[0];
+    st->b2 = tot[1];
+    st->res = (tot[1] > 0.0) ? sqrt(tot[0] / tot[1]) : 0.0;
+    st->done = 0;
+    st->mv_t_on = 1;
+    if (tot[1] == 0.0 || st->res <= st->tol) finish(st, BEM_OK);
+  }
+}
+
+template <typename T>
+__global__ void k_lin_alpha(const T* __restrict__ s, const T* __restrict__ q, const uint8_t* __restrict__ C,
+                            double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  if (st->done) return;
+  Acc<T> a;
+  GRID_STRIDE(i, n) if (C[i]) a.add(s[i] * q[i]);
+  double v[1] = {a.value()}, tot[1];
+  if (grid_reduce<1>(v, partials, ticket, tot)) {
+    const double alpha = st->rr / tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(alpha)) {
+      finish(st, BEM_ENAN);
+      return;
+    }
+    st->alpha = alpha;
+  }
+}
+
+template <typename T>
+__global__ void k_lin_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ s, const T* __restrict__ q,
+                             const uint8_t* __restrict__ C, double* partials, unsigned int* ticket, SolveState* st,
+                             size_t n) {
+  if (st->done) return;
+  const T alpha = (T)st->alpha;
+  Acc<T> arr;
+  GRID_STRIDE(i, n) {
+    if (C[i]) {
+      x[i] += alpha * s[i];
+      const T ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      arr.add(ri * ri);
+    }
+  }
+  double v[1] = {arr.value()}, tot[1];
+  if (grid_reduce<1>(v, partials, ticket, tot)) {
+    st->beta = tot[0] / st->rr;
+    st->rr = tot[0];
+    st->iter += 1;
+    st->matvecs += 1;
+    st->res = sqrt(tot[0] / st->b2);
+    if (!isfinite(st->res)) {
+      finish(st, BEM_ENAN);
+    } else if (st->res <= st->tol) {
+      finish(st, BEM_OK);
+    } else if (st->iter >= st->max_iter) {
+      finish(st, BEM_ENOCONV);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_lin_dir(const T* __restrict__ r, T* __restrict__ s, const uint8_t* __restrict__ C,
+                          const SolveState* st, size_t n) {
+  if (st->done) return;
+  const T beta = (T)st->beta;
+  GRID_STRIDE(i, n) s[i] = C[i] ? r[i] + beta * s[i] : (T)0;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Contact-area update (Sec. 2): with g = K x + f - d, cells outside C with g < 0
+// join; cells of C with a 4-neighbour outside C (window edge = outside) whose
+// tension -x exceeds sigma_c (compared in double) leave.  Writes the new mask,
+// zeroes x outside it, counts both moves and hashes the new set.
+template <typename T>
+__global__ void k_detach(T* __restrict__ x, const T* __restrict__ u, const T* __restrict__ f,
+                         const uint8_t* __restrict__ C, uint8_t* __restrict__ Cn, int logN, double* partials,
+                         unsigned int* ticket, SolveState* st) {
+  const int N = 1 << logN;
+  const size_t n = (size_t)N * N;
+  const double d = st->d, sc = st->sig_c;
+  double nadd = 0.0, ndet = 0.0, ncon = 0.0;
+  uint64_t hsh = 0;
+  Acc<T> ap;
+  GRID_STRIDE(i, n) {
+    const int r = (int)(i >> logN), c = (int)(i & (N - 1));
+    const bool in = C[i] != 0;
+    bool out_in = in;
+    if (!in) {
+      const T gi = u[i] + (T)((double)f[i] - d);
+      if (gi < (T)0) {
+        out_in = true;
+        nadd += 1.0;
+      }
+    } else {
+      const bool inner = (r > 0 && C[i - N]) && (r < N - 1 && C[i + N]) && (c > 0 && C[i - 1]) &&
+                         (c < N - 1 && C[i + 1]);
+      if (!inner && -(double)x[i] > sc) {
+        out_in = false;
+        ndet += 1.0;
+      }
+    }
+    Cn[i] = out_in ? 1 : 0;
+    if (!out_in) x[i] = (T)0;
+    if (out_in) {
+      ncon += 1.0;
+      hsh += mix64((uint64_t)i);
+      ap.add(x[i]);
+    }
+  }
+  // hash: sum of mixed indices (order-free), carried as two exact 32-bit halves in double
+  double v[6] = {nadd, ndet, ncon, ap.value(), (double)(uint32_t)(hsh & 0xffffffffu), (double)(uint32_t)(hsh >> 32)};
+  double tot[6];
+  if (grid_reduce<6>(v, partials, ticket, tot)) {
+    st->n_add = (int)tot[0];
+    st->n_detach = (int)tot[1];
+    st->n_c = (int)tot[2];
+    st->sum_p = tot[3];
+    const uint64_t lo = (uint64_t)tot[4], hi = (uint64_t)tot[5];
+    st->mask_hash = lo + (hi << 32);
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ x, double value, size_t n) {
+  GRID_STRIDE(i, n) x[i] = (T)value;
+}
+
+// Warm start: p = max(p, 0); under force control the pending rescale s = F/(delta^2 sum p)
+// is left in the state for the first gap refresh to apply.
+template <typename T>
+__global__ void k_init_clamp(T* __restrict__ p, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  Acc<T> a;
+  GRID_STRIDE(i, n) {
+    const T v = p[i] > (T)0 ? p[i] : (T)0;
+    p[i] = v;
+    a.add(v);
+  }
+  double v[1] = {a.value()}, tot[1];
+  if (grid_reduce<1>(v, partials, ticket, tot)) {
+    if (st->control == BEM_CTRL_FORCE) {
+      if (tot[0] > 0.0) st->scale = st->target / (st->delta2 * tot[0]);
+      else finish(st, BEM_EINVAL);
+    }
+  }
+}
+
+template <typename T>
+bem_status read_state(bem_kernel_s* k, cudaStream_t s) {
+  BEM_CUDA_TRY(cudaMemcpyAsync(k->ws.state_host, k->ws.state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+struct Ctx {
+  size_t n;
+  int rb, eb;
+};
+
+template <typename T>
+Ctx ctx_of(const bem_kernel_s* k) {
+  Ctx c;
+  c.n = (size_t)k->N * k->N;
+  c.rb = red_blocks(c.n);
+  c.eb = (int)std::min<size_t>((c.n + NTHREADS - 1) / NTHREADS, 152 * 16);
+  return c;
+}
+
+template <typename T>
+bem_status final_stats(bem_kernel_s* k, const T* p, double d, double* out5, cudaStream_t s) {
+  const Ctx c = ctx_of<T>(k);
+  DV<T> v = dv<T>(k);
+  launch_matvec<T>(k, p, v.u, s, nullptr);
+  double* dout = k->ws.partials + 7 * RED_MAX_BLOCKS;
+  k_final_stats<T><<<c.rb, NTHREADS, 0, s>>>(p, v.u, v.f, k->ws.partials, k->ws.ticket, d, dout, c.n);
+  note_launches(1);
+  BEM_CUDA_TRY(cudaGetLastError());
+  BEM_CUDA_TRY(cudaMemcpyAsync(out5, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+template <typename T>
+bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cudaStream_t s) {
+  const Ctx c = ctx_of<T>(k);
+  DV<T> v = dv<T>(k);
+  SolveState* st = k->ws.state;
+  SolveState* hs = k->ws.state_host;
+  double* part = k->ws.partials;
+  unsigned int* tk = k->ws.ticket;
+  const bool force = prob->control == BEM_CTRL_FORCE;
+  const double delta2 = k->desc.delta * k->desc.delta;
+
+  SolveState init{};
+  init.d = force ? 0.0 : prob->target;
+  init.Gold = 1.0;
+  init.flag = 0.0;
+  init.scale = 1.0;
+  init.target = prob->target;
+  init.delta2 = delta2;
+  init.tol = prob->tol;
+  init.control = prob->control;
+  init.max_iter = prob->max_iter;
+  init.n_neg = 1;  // no convergence test passes before one full iteration
+  init.status = BEM_OK;
+  init.mv_t_on = 1;
+  BEM_CUDA_TRY(cudaMemsetAsync(v.t, 0, c.n * sizeof(T), s));
+  if (pinit != nullptr || force) {
+    init.refresh = 1;
+    init.mv_p_on = 1;
+  }
+  *hs = init;
+  BEM_CUDA_TRY(cudaMemcpyAsync(st, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+  if (pinit != nullptr) {
+    if (pinit != v.p) BEM_CUDA_TRY(cudaMemcpyAsync(v.p, pinit, c.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    k_init_clamp<T><<<c.rb, NTHREADS, 0, s>>>(v.p, part, tk, st, c.n);
+    note_launches(1);
+  } else if (force) {
+    k_fill<T><<<c.eb, NTHREADS, 0, s>>>(v.p, prob->target / (delta2 * (double)c.n), c.n);
+    note_launches(1);
+  } else {
+    k_init_q<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.x, prob->target, c.n);
+    note_launches(1);
+    launch_matvec<T>(k, v.x, v.u, s, nullptr);
+    k_init_scale<T><<<c.rb, NTHREADS, 0, s>>>(v.f, v.x, v.u, part, tk, st, c.n);
+    note_launches(1);
+    k_init_apply<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.x, v.u, v.p, v.g, st, c.n);
+    note_launches(1);
+  }
+  BEM_CUDA_TRY(cudaGetLastError());
+  int extra_mv = (pinit == nullptr && !force) ? 1 : 0;
+
+  for (;;) {
+    for (int it = 0; it < CHUNK; ++it) {
+      launch_matvec<T>(k, v.p, v.u, s, &st->mv_p_on);
+      k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, st, c.n);
+      note_launches(1);
+      k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, part, tk, st, c.n);
+      note_launches(1);
+      k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
+      note_launches(1);
+      launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
+      k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
+      note_launches(1);
+      k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
+      note_launches(1);
+    }
+    BEM_CUDA_TRY(cudaGetLastError());
+    bem_status e = read_state<T>(k, s);
+    if (e != BEM_OK) return e;
+    if (hs->done) break;
+  }
+  hs->matvecs += extra_mv + ((pinit != nullptr || force) ? 1 : 0);
+  return BEM_OK;
+}
+
+template <typename T>
+bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit, uint8_t* mask_dev,
+                        int* outer_out, int* iters_out, int* mv_out, double* res_out, cudaStream_t s) {
+  const Ctx c = ctx_of<T>(k);
+  DV<T> v = dv<T>(k);
+  SolveState* st = k->ws.state;
+  SolveState* hs = k->ws.state_host;
+  double* part = k->ws.partials;
+  unsigned int* tk = k->ws.ticket;
+  uint8_t* C = mask_dev;
+  uint8_t* Cn = k->ws.mask + c.n;
+  const double delta = k->desc.delta;
+  const double Es1 = k->desc.E1 / (1.0 - k->desc.nu1 * k->desc.nu1);
+  // Eq. (12): sigma_c = sqrt(E1* dgamma / (0.473201 delta))
+  const double sig_c = sqrt(Es1 * prob->dgamma / (0.473201 * delta));
+
+  // x holds the pressure of the fixed-area solve
+  if (pinit != nullptr) {
+    if (pinit != v.x) BEM_CUDA_TRY(cudaMemcpyAsync(v.x, pinit, c.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  } else {
+    BEM_CUDA_TRY(cudaMemsetAsync(v.x, 0, c.n * sizeof(T), s));
+  }
+  k_mask_restrict<T><<<c.eb, NTHREADS, 0, s>>>(v.x, C, c.n);
+  note_launches(1);
+
+  std::unordered_set<uint64_t> seen;
+  int iters = 0, mv = 0, outer = 0;
+  double res = 0.0;
+  const int max_outer = 1000;
+  for (outer = 1; outer <= max_outer; ++outer) {
+    SolveState init{};
+    init.d = prob->target;
+    init.tol = prob->tol;
+    init.max_iter = prob->max_iter;
+    init.sig_c = sig_c;
+    init.delta2 = delta * delta;
+    init.status = BEM_OK;
+    init.mv_t_on = 1;
+    *hs = init;
+    BEM_CUDA_TRY(cudaMemcpyAsync(st, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    // CG on K_CC x = (d - f)_C
+    launch_matvec<T>(k, v.x, v.u, s, nullptr);
+    k_lin_init<T><<<c.rb, NTHREADS, 0, s>>>(v.u, v.f, C, v.r, v.t, part, tk, st, c.n);
+    note_launches(1);
+    mv += 1;
+    for (;;) {
+      for (int it = 0; it < CHUNK; ++it) {
+        launch_matvec<T>(k, v.t, v.g, s, &st->mv_t_on);
+        k_lin_alpha<T><<<c.rb, NTHREADS, 0, s>>>(v.t, v.g, C, part, tk, st, c.n);
+        note_launches(1);
+        k_lin_update<T><<<c.rb, NTHREADS, 0, s>>>(v.x, v.r, v.t, v.g, C, part, tk, st, c.n);
+        note_launches(1);
+        k_lin_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.r, v.t, C, st, c.n);
+        note_launches(1);
+      }
+      BEM_CUDA_TRY(cudaGetLastError());
+      bem_status e = read_state<T>(k, s);
+      if (e != BEM_OK) return e;
+      if (hs->done) break;
+    }
+    iters += hs->iter;
+    mv += hs->matvecs;
+    res = hs->res;
+    if (hs->status != BEM_OK) {
+      *outer_out = outer; *iters_out = iters; *mv_out = mv; *res_out = res;
+      return (bem_status)hs->status;
+    }
+    // area update from the fresh gap
+    launch_matvec<T>(k, v.x, v.u, s, nullptr);
+    mv += 1;
+    k_detach<T><<<c.rb, NTHREADS, 0, s>>>(v.x, v.u, v.f, C, Cn, k->logN, part, tk, st);
+    note_launches(1);
+    BEM_CUDA_TRY(cudaGetLastError());
+    bem_status e = read_state<T>(k, s);
+    if (e != BEM_OK) return e;
+    if (hs->n_add == 0 && hs->n_detach == 0) break;
+    if (!seen.insert(hs->mask_hash).second) {
+      *outer_out = outer; *iters_out = iters; *mv_out = mv; *res_out = res;
+      set_error("adhesive contact area revisited an earlier state");
+      return BEM_ECYCLE;
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(C, Cn, c.n, cudaMemcpyDeviceToDevice, s));
+  }
+  *outer_out = std::min(outer, max_outer);
+  *iters_out = iters;
+  *mv_out = mv;
+  *res_out = res;
+  if (outer > max_outer) {
+    set_error("adhesive outer loop did not settle");
+    return BEM_ENOCONV;
+  }
+  return BEM_OK;
+}
+
+template <typename T>
+__global__ void k_nonfinite(const T* __restrict__ a, const T* __restrict__ b, double* partials, unsigned int* ticket,
+                            double* out, size_t n) {
+  double cnt = 0.0;
+  GRID_STRIDE(i, n) {
+    if (!isfinite((double)a[i])) cnt += 1.0;
+    if (b != nullptr && !isfinite((double)b[i])) cnt += 1.0;
+  }
+  double v[1] = {cnt}, tot[1];
+  if (grid_reduce<1>(v, partials, ticket, tot)) out[0] = tot[0];
+}
+
+template <typename T>
+bem_status solve_typed(bem_kernel_s* k, const bem_problem* prob, const T* f, const T* pinit, uint8_t* mask,
+                       T* p_out, bem_result* res, cudaStream_t s) {
+  DV<T> v = dv<T>(k);
+  const size_t n = (size_t)k->N * k->N;
+  const double delta2 = k->desc.delta * k->desc.delta;
+  if (f != v.f) BEM_CUDA_TRY(cudaMemcpyAsync(v.f, f, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  *res = bem_result{};
+  {
+    const Ctx c = ctx_of<T>(k);
+    double* dout = k->ws.partials + 7 * RED_MAX_BLOCKS;
+    double bad = 0.0;
+    k_nonfinite<T><<<c.rb, NTHREADS, 0, s>>>(v.f, pinit, k->ws.partials, k->ws.ticket, dout, n);
+    note_launches(1);
+    BEM_CUDA_TRY(cudaGetLastError());
+    BEM_CUDA_TRY(cudaMemcpyAsync(&bad, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad > 0.0) {
+      set_error("non-finite value in the height map or the warm start");
+      res->status = BEM_ENAN;
+      return BEM_ENAN;
+    }
+  }
+  bem_status st = BEM_OK;
+  double d = prob->target;
+  const T* psol = nullptr;
+  if (prob->dgamma > 0.0) {
+    int outer = 0, iters = 0, mv = 0;
+    double r = 0.0;
+    st = run_adhesive<T>(k, prob, pinit, mask, &outer, &iters, &mv, &r, s);
+    res->outer_iters = outer;
+    res->iters = iters;
+    res->matvecs = mv;
+    res->residual = r;
+    psol = v.x;
+  } else {
+    st = run_pk<T>(k, prob, pinit, s);
+    const SolveState* hs = k->ws.state_host;
+    res->iters = hs->iter;
+    res->outer_iters = 1;
+    res->matvecs = hs->matvecs;
+    res->residual = hs->res;
+    d = hs->d;
+    if (st == BEM_OK) st = (bem_status)hs->status;
+    psol = v.p;
+  }
+  double fs[5];
+  bem_status e = final_stats<T>(k, psol, d, fs, s);
+  if (e != BEM_OK) return e;
+  res->matvecs += 1;
+  const double n_c = fs[3];
+  double gbar = 0.0;
+  if (prob->dgamma == 0.0 && prob->control == BEM_CTRL_FORCE && n_c > 0) gbar = fs[0] / n_c;
+  const double G = fmax(fs[1] - n_c * gbar * gbar, 0.0);
+  res->err_est = (fs[2] > 0.0) ? sqrt(G / fs[2]) : 0.0;
+  res->force = delta2 * fs[4];
+  res->depth = d;
+  res->n_contact = (int)n_c;
+  res->area = delta2 * n_c;
+  res->a_eq = sqrt(res->area / M_PI);
+  res->status = st;
+  if (p_out != nullptr && p_out != psol)
+    BEM_CUDA_TRY(cudaMemcpyAsync(p_out, psol, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  if (st == BEM_ENOCONV) set_error("iteration limit reached before the tolerance");
+  if (st == BEM_ENAN) set_error("non-finite or non-positive curvature in CG");
+  return st;
+}
+
+}  // namespace
+
+bem_status solve_contact_device(bem_kernel_s* k, const bem_problem* prob, const void* f, const void* pinit,
+                                uint8_t* mask, void* p_out, bem_result* res, cudaStream_t s) {
+  if (k->prec == BEM_FP64)
+    return solve_typed<double>(k, prob, (const double*)f, (const double*)pinit, mask, (double*)p_out, res, s);
+  return solve_typed<float>(k, prob, (const float*)f, (const float*)pinit, mask, (float*)p_out, res, s);
+}
+
+}  // namespace bem

@@ -11,3 +11,19 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libbem.so")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+@pytest.fixture(scope="session")
+def bemlib():
+    """Builds (if needed) and loads libbem.so."""
+    from paper_1807_01885_gb300 import bem, build
+    build.build()
+    return bem.load()
+
+
+@pytest.fixture(scope="session")
+def cuda(bemlib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a gpu-marked test ran without a CUDA device")
+    return torch.device("cuda:0")

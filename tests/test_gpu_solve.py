@@ -1,0 +1,181 @@
+"""GPU parity of the contact solves against the oracle (same seeded inputs).
+
+Tolerances: FP64 path rel-L2 1e-10 on pressure and force; FP32 path (float FFT and
+vectors, double reductions) 2e-4 on pressure, 1e-5 on force.  Both sides converge
+to a residual far below these, so the comparison is of the unique solution."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import contact, operator
+from paper_1807_01885_gb300 import bem, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def oracle_mv(N, delta, h, E1, nu1, E2, nu2):
+    Kg = operator.khat_grid(N, delta, h, E1, nu1, E2, nu2)
+    return lambda p: operator.matvec_fft(Kg, p)
+
+
+# config-1-like: sphere R = 1, a_H = 0.01, L = 4 a_H, h = a_H, E1/E2 = 4, nu = 0.3
+SPHERE = dict(N=64, R=1.0, d=1e-4, h=0.01, E1=4.0, nu1=0.3, E2=1.0, nu2=0.3)
+
+
+def sphere_case(N=64):
+    c = dict(SPHERE)
+    c["N"] = N
+    c["delta"] = 4 * 0.01 / N
+    f = inputs.sphere_height(N, c["delta"], c["R"])
+    return c, f
+
+
+@pytest.mark.parametrize("N", [16, 64, 128])
+def test_sphere_depth_control_fp64(cuda, N):
+    c, f = sphere_case(N)
+    mv = oracle_mv(N, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"])
+    ref = contact.solve_nonadhesive(mv, f, c["delta"], "depth", c["d"], tol=1e-13)
+    with bem.Kernel(N, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"]) as k:
+        p, res = k.solve(torch.tensor(f, device=cuda), "depth", c["d"], tol=1e-13)
+    assert res["status"] == 0
+    assert rel(p.cpu().numpy(), ref["p"]) < 1e-10
+    assert abs(res["force"] / ref["force"] - 1) < 1e-10
+    assert res["n_contact"] == ref["n_contact"]
+
+
+def test_sphere_force_control_fp64(cuda):
+    c, f = sphere_case(64)
+    mv = oracle_mv(64, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"])
+    F = 2e-5
+    ref = contact.solve_nonadhesive(mv, f, c["delta"], "force", F, tol=1e-13)
+    with bem.Kernel(64, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"]) as k:
+        p, res = k.solve(torch.tensor(f, device=cuda), "force", F, tol=1e-13)
+    assert res["status"] == 0
+    assert rel(p.cpu().numpy(), ref["p"]) < 1e-10
+    assert res["force"] == pytest.approx(F, rel=1e-12)
+    assert res["depth"] == pytest.approx(ref["d"], rel=1e-9)
+
+
+@pytest.mark.parametrize("control,target", [("depth", 1e-4), ("force", 2e-5)])
+def test_sphere_fp32(cuda, control, target):
+    c, f = sphere_case(128)
+    mv = oracle_mv(128, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"])
+    ref = contact.solve_nonadhesive(mv, f, c["delta"], control, target, tol=1e-13)
+    with bem.Kernel(128, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"], precision="fp32") as k:
+        p, res = k.solve(torch.tensor(f, device=cuda, dtype=torch.float32), control, target, tol=1e-8)
+    assert res["status"] == 0
+    assert rel(p.double().cpu().numpy(), ref["p"]) < 2e-4
+    assert abs(res["force"] / ref["force"] - 1) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rough_surface_force_control(cuda, precision):
+    N = 128
+    inst = inputs.batch_instance(20260000 + 5, sizes=(N,))
+    mv = oracle_mv(N, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"])
+    ref = contact.solve_nonadhesive(mv, inst["height"], inst["delta"], "force", inst["force"], tol=1e-13)
+    with bem.Kernel(N, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"],
+                    precision=precision) as k:
+        f = torch.tensor(inst["height"], device=cuda, dtype=k.torch_dtype)
+        p, res = k.solve(f, "force", inst["force"], tol=1e-13 if precision == "fp64" else 1e-8, max_iter=20000)
+    assert res["status"] == 0
+    tol_p = 1e-10 if precision == "fp64" else 2e-4
+    assert rel(p.double().cpu().numpy(), ref["p"]) < tol_p
+
+
+def test_flat_punch_and_host_arguments(cuda):
+    """Flat punch, rigid base (the Fig. 3 geometry at small size), host arrays in and out."""
+    N, delta = 64, 1.0
+    a, h = 16.0, 2.0
+    f = inputs.flat_punch_height(N, delta, a)
+    mv = oracle_mv(N, delta, h, 1.0, 0.3, np.inf, 0.3)
+    ref = contact.solve_nonadhesive(mv, f, delta, "depth", 1e-3, tol=1e-13)
+    with bem.Kernel(N, delta, h, 1.0, 0.3, np.inf, 0.3) as k:
+        p, res = k.solve(f.copy(), "depth", 1e-3, tol=1e-13)
+    assert isinstance(p, np.ndarray)
+    assert rel(p, ref["p"]) < 1e-10
+
+
+def test_no_contact_and_statuses(cuda):
+    c, f = sphere_case(32)
+    with bem.Kernel(32, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"]) as k:
+        ft = torch.tensor(f, device=cuda)
+        p, res = k.solve(ft, "depth", -1e-4, tol=1e-12)          # indenter above the surface
+        assert res["status"] == 0 and res["force"] == 0.0 and res["n_contact"] == 0
+        assert float(p.abs().max()) == 0.0
+        p, res = k.solve(ft, "depth", 1e-4, tol=1e-14, max_iter=2)
+        assert res["status"] == bem.BEM_ENOCONV
+        with pytest.raises(bem.BemError):
+            k.solve(ft, "force", -1.0)
+        fn = ft.clone()
+        fn[3, 3] = float("nan")
+        with pytest.raises(bem.BemError) as e:
+            k.solve(fn, "depth", 1e-4, tol=1e-12)
+        assert e.value.status == bem.BEM_ENAN
+
+
+def test_warm_start_converges_faster(cuda):
+    c, f = sphere_case(128)
+    with bem.Kernel(128, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"]) as k:
+        ft = torch.tensor(f, device=cuda)
+        p0, r0 = k.solve(ft, "depth", c["d"], tol=1e-12)
+        p1, r1 = k.solve(ft, "depth", c["d"], tol=1e-12, p_init=p0.clone())
+    assert r1["status"] == 0 and r1["iters"] < max(2, r0["iters"] // 4)
+    assert rel(p1.cpu().numpy(), p0.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adhesive_ramp_parity(cuda, precision):
+    """Homogeneous JKR-type pull-off (Sec. 2 procedure, Eq. 12) on both sides:
+    identical contact areas at every step, forces within the path tolerance."""
+    N, R, E, nu = 64, 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Es = E / (1 - nu * nu)
+    a_d = 5 * delta
+    dg = a_d ** 3 * 8 * Es / (np.pi * R * R)
+    a_F = 9 ** (1 / 3) * a_d
+    f = inputs.sphere_height(N, delta, R)
+    d_max = (1.4 * a_F) ** 2 / R
+    depths = np.concatenate([np.linspace(0, d_max, 4), np.linspace(d_max, -0.006, 24)])
+    mv = oracle_mv(N, delta, np.inf, E, nu, E, nu)
+    sc = contact.sigma_c(E, nu, dg, delta)
+    ref = contact.adhesive_ramp(mv, f, delta, depths, sc, tol=1e-12)
+    with bem.Kernel(N, delta, np.inf, E, nu, E, nu, precision=precision) as k:
+        ft = torch.tensor(f, device=cuda, dtype=k.torch_dtype)
+        mask = torch.zeros((N, N), dtype=torch.uint8, device=cuda)
+        p = torch.zeros_like(ft)
+        for i, d in enumerate(depths):
+            p_new, res = k.solve(ft, "depth", float(d), dgamma=dg, tol=1e-12 if precision == "fp64" else 1e-7,
+                                 p_init=p, contact_mask=mask)
+            p = p_new.clone()
+            assert res["status"] == 0
+            assert res["n_contact"] == ref[i]["n_contact"], i
+            assert np.array_equal(mask.cpu().numpy().astype(bool), ref[i]["C"]), i
+            ftol = 1e-10 if precision == "fp64" else 1e-5
+            assert abs(res["force"] - ref[i]["force"]) <= ftol * max(abs(ref[i]["force"]), 1e-3 * Es * a_d ** 2)
+
+
+def test_batch_matches_single_solves(cuda):
+    insts = [inputs.batch_instance(20260000 + i, sizes=(64, 128)) for i in range(4)]
+    ks, probs, outs, hts, singles = [], [], [], [], []
+    for inst in insts:
+        k = bem.Kernel(inst["N"], inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"],
+                       precision="fp32")
+        ht = torch.tensor(inst["height"], device=cuda, dtype=torch.float32)
+        p, r = k.solve(ht, "force", inst["force"], tol=1e-8)
+        singles.append((p.clone(), r))
+        ks.append(k)
+        hts.append(ht)
+        outs.append(torch.empty_like(ht))
+        probs.append(bem.make_problem(ht, bem.BEM_CTRL_FORCE, inst["force"], tol=1e-8))
+    st, res = bem.bem_solve_batch([k.handle for k in ks], probs, outs)
+    assert st == 0
+    for (p, r), o, rb in zip(singles, outs, res):
+        assert torch.equal(p, o)
+        assert rb["force"] == r["force"] and rb["iters"] == r["iters"]
+    for k in ks:
+        k.close()
