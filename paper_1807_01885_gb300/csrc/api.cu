@@ -1,6 +1,7 @@
 // C ABI of libbem.so (declared in include/bem.h): argument checks, workspace
 // ownership, host/device argument staging, error reporting.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -76,6 +77,8 @@ void free_ws(bem_kernel_s* k) {
   cudaFree(w.table);
   cudaFree(w.table64);
   cudaFree(w.tw);
+  cudaFree(w.twr);
+  cudaFree(w.twc);
   cudaFree(w.vec);
   cudaFree(w.mask);
   cudaFree(w.partials);
@@ -171,6 +174,14 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
   k->prec = desc->precision;
   k->elem = (k->prec == BEM_FP64) ? sizeof(double) : sizeof(float);
   cudaGetDevice(&k->dev);
+  {
+    const char* alt = getenv("BEM_COL_RADIX_ALT");
+    k->col_radix_alt = (alt != nullptr && alt[0] == '1') ? 1 : 0;
+    const char* ralt = getenv("BEM_ROW_RADIX_ALT");
+    k->row_radix_alt = (ralt != nullptr && ralt[0] == '1') ? 1 : 0;
+    const char* cp = getenv("BEM_COL_PERSIST");
+    k->col_persist = (cp != nullptr && cp[0] == '1') ? 1 : 0;
+  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t n = (size_t)k->N * k->N;
   Workspace& w = k->ws;
@@ -186,6 +197,10 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
   if ((e = cudaMalloc((void**)&w.table64, (size_t)(k->N + 1) * (k->N + 1) * sizeof(double))) != cudaSuccess)
     return fail(e, "cudaMalloc(table64)");
   if ((e = cudaMalloc(&w.tw, (size_t)k->M * 2 * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(tw)");
+  if ((e = cudaMalloc(&w.twr, (size_t)stage_tw_count(k->logN) * 2 * k->elem)) != cudaSuccess)
+    return fail(e, "cudaMalloc(twr)");
+  if ((e = cudaMalloc(&w.twc, (size_t)stage_tw_count(k->logN + 1) * 2 * k->elem)) != cudaSuccess)
+    return fail(e, "cudaMalloc(twc)");
   if ((e = cudaMalloc(&w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
   if ((e = cudaMalloc((void**)&w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
   if ((e = cudaMalloc((void**)&w.partials, 8 * 1024 * sizeof(double))) != cudaSuccess)

@@ -55,6 +55,8 @@ struct SolveState {
   double res;        // relative residual
   double sum_p;      // sum of pressures after the update
   double scale;      // pending load-control rescale of p (1 = none)
+  double uscale;     // rms displacement over the contact set (noise thresholds)
+  double pscale;     // mean pressure over the contact set
   double target;     // F under force control
   double delta2;     // delta^2
   double tol;
@@ -83,6 +85,8 @@ struct Workspace {
   void* table = nullptr;     // (N/TC + 1) * (N+1) * TC real, blocked, scaled by 1/M^2
   double* table64 = nullptr; // (N+1)^2 doubles, unscaled, row-major
   void* tw = nullptr;        // M complex: e^{-2 pi i k / M}
+  void* twr = nullptr;       // stage twiddles of the length-N register FFT (rows)
+  void* twc = nullptr;       // stage twiddles of the length-2N register FFT (columns)
   void* vec = nullptr;       // solver vectors: p, g, t, r, u, f, x (N*N each)
   uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy
   double* partials = nullptr;// per-block partial sums
@@ -101,6 +105,9 @@ struct bem_kernel_s {
   int prec;       // BEM_FP64 / BEM_FP32
   size_t elem;    // sizeof(real)
   int dev;
+  int col_radix_alt;   // 1: alternative radix for the column pass (set from BEM_COL_RADIX_ALT)
+  int row_radix_alt;   // 1: alternative radix for the row passes (set from BEM_ROW_RADIX_ALT)
+  int col_persist;     // 1: persistent, prefetching column pass (BEM_COL_PERSIST=1)
   bem::Workspace ws;
 };
 
@@ -119,6 +126,12 @@ void launch_matvec(const bem_kernel_s* k, const T* p, T* u, cudaStream_t s, cons
 template <typename T>
 void launch_pass(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStream_t s);
 size_t spec_bytes(const bem_kernel_s* k);
+// matvec_f32.cu / matvec_f64.cu (N >= 16)
+template <typename T>
+void reg_pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s, const int* skip);
+template <typename T>
+void reg_twiddles(const bem_kernel_s* k, cudaStream_t s);
+int stage_tw_count(int logl);
 size_t table_bytes(const bem_kernel_s* k);
 
 // solve.cu

@@ -73,6 +73,18 @@ __global__ void k_table_block(const double* __restrict__ t64, T* __restrict__ ta
   }
 }
 
+// Square copy in the path precision, scaled by 1/M^2, rows padded to N + 4 entries.
+// K depends on i^2 + j^2 only, so entry (i, j) is also entry (j, i): the values of
+// frequency column j form row j here.
+template <typename T>
+__global__ void k_table_square(const double* __restrict__ t64, T* __restrict__ tab, int N, double scale) {
+  const size_t total = (size_t)(N + 1) * (N + 4);
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx / (N + 4), j = idx % (N + 4);
+    tab[idx] = (j <= (size_t)N) ? (T)(t64[i * (N + 1) + j] * scale) : (T)0;
+  }
+}
+
 template <typename T>
 __global__ void k_twiddles(cplx<T>* __restrict__ tw, int M) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
@@ -103,11 +115,19 @@ static void layered_constants(const bem_kernel_desc& d, double* A, double* B, do
   *D = (al + (3.0 - 4.0 * n2) * be) * ((3.0 - 4.0 * n1) * al + be);
 }
 
+// Upper bound on the stage twiddle entries of a length-2^logl register FFT: the
+// stage tables hold sum_{s>=1} R_s Ns_s = sum_{s>=1} Ns_{s+1} < 2L values.
+int stage_tw_count(int logl) { return 2 << logl; }
+
 size_t spec_bytes(const bem_kernel_s* k) {
   return (size_t)(k->N / TC + 1) * k->N * TC * 2 * k->elem;
 }
 size_t table_bytes(const bem_kernel_s* k) {
-  return (size_t)(k->N / TC + 1) * (k->N + 1) * TC * k->elem;
+  // blocked layout (N < 16 path) or the square table (register path, rows of N + 4
+  // so that every row starts on a 16-byte boundary), whichever is larger
+  const size_t blocked = (size_t)(k->N / TC + 1) * (k->N + 1) * TC;
+  const size_t square = (size_t)(k->N + 1) * (k->N + 4);
+  return (blocked > square ? blocked : square) * k->elem;
 }
 
 bem_status build_table(bem_kernel_s* k, cudaStream_t s) {
@@ -134,11 +154,15 @@ bem_status build_table(bem_kernel_s* k, cudaStream_t s) {
   BEM_CUDA_TRY(cudaGetLastError());
   const double scale = 1.0 / ((double)k->M * (double)k->M);
   if (k->prec == BEM_FP64) {
-    k_table_block<double><<<256, 256, 0, s>>>(k->ws.table64, (double*)k->ws.table, k->N, scale);
+    if (k->logN >= 4) k_table_square<double><<<256, 256, 0, s>>>(k->ws.table64, (double*)k->ws.table, k->N, scale);
+    else k_table_block<double><<<256, 256, 0, s>>>(k->ws.table64, (double*)k->ws.table, k->N, scale);
     k_twiddles<double><<<(k->M + 255) / 256, 256, 0, s>>>((double2*)k->ws.tw, k->M);
+    if (k->logN >= 4) reg_twiddles<double>(k, s);
   } else {
-    k_table_block<float><<<256, 256, 0, s>>>(k->ws.table64, (float*)k->ws.table, k->N, scale);
+    if (k->logN >= 4) k_table_square<float><<<256, 256, 0, s>>>(k->ws.table64, (float*)k->ws.table, k->N, scale);
+    else k_table_block<float><<<256, 256, 0, s>>>(k->ws.table64, (float*)k->ws.table, k->N, scale);
     k_twiddles<float><<<(k->M + 255) / 256, 256, 0, s>>>((float2*)k->ws.tw, k->M);
+    if (k->logN >= 4) reg_twiddles<float>(k, s);
   }
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
@@ -287,6 +311,11 @@ static void pass_impl(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStr
   const size_t smem_col = (size_t)4 * N * sizeof(C);
   C* spec = (C*)k->ws.spec;
   const C* tw = (const C*)k->ws.tw;
+  if (k->logN >= 4) {
+    reg_pass<T>(k, pass, p, u, s, skip);
+    note_launches(1);
+    return;
+  }
   if (pass == 0) k_row_fwd<T, TR><<<N / TR, NTHREADS, smem_row, s>>>(p, spec, tw, logN, skip);
   if (pass == 1) k_col<T><<<N / TC + 1, NTHREADS, smem_col, s>>>(spec, (const T*)k->ws.table, tw, logN, skip);
   if (pass == 2) k_row_inv<T, TR><<<N / TR, NTHREADS, smem_row, s>>>(spec, u, tw, logN, skip);

@@ -39,13 +39,33 @@ DV<T> dv(const bem_kernel_s* k) {
 }
 
 int red_blocks(size_t n) {
-  size_t b = (n + NTHREADS * 8 - 1) / (NTHREADS * 8);
+  size_t b = (n + NTHREADS * 16 - 1) / (NTHREADS * 16);
   b = std::max<size_t>(1, std::min<size_t>(b, RED_MAX_BLOCKS));
   return (int)b;
 }
 
 #define GRID_STRIDE(i, n) \
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+// Four consecutive elements per access (16-byte loads for float, two for double).
+#define VEC_LOOP(i4, n) \
+  for (size_t i4 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i4 < (n) / 4; i4 += (size_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void ld4(const float* p, size_t i4, float (&o)[4]) {
+  const float4 v = reinterpret_cast<const float4*>(p)[i4];
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, size_t i4, double (&o)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[2 * i4], b = reinterpret_cast<const double2*>(p)[2 * i4 + 1];
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, size_t i4, const float (&o)[4]) {
+  reinterpret_cast<float4*>(p)[i4] = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4(double* p, size_t i4, const double (&o)[4]) {
+  reinterpret_cast<double2*>(p)[2 * i4] = make_double2(o[0], o[1]);
+  reinterpret_cast<double2*>(p)[2 * i4 + 1] = make_double2(o[2], o[3]);
+}
 
 __device__ __forceinline__ void finish(SolveState* st, int status) {
   st->done = 1;
@@ -61,7 +81,8 @@ __device__ __forceinline__ void finish(SolveState* st, int status) {
 // factor s = <q, d - f> / <q, K q>; the gap then follows from u = K q as s u + f - d.
 template <typename T>
 __global__ void k_init_q(const T* __restrict__ f, T* __restrict__ q, double d, size_t n) {
-  GRID_STRIDE(i, n) q[i] = (T)fmax((double)d - (double)f[i], 0.0);
+  const T dT = (T)d;
+  GRID_STRIDE(i, n) q[i] = (dT - f[i] > (T)0 ? dT - f[i] : (T)0);
 }
 
 template <typename T>
@@ -85,9 +106,10 @@ __global__ void k_init_apply(const T* __restrict__ f, const T* __restrict__ q, c
                              T* __restrict__ p, T* __restrict__ g, const SolveState* st, size_t n) {
   const T s = (T)st->scale;
   const double d = st->d;
+  const T dT = (T)d;
   GRID_STRIDE(i, n) {
     p[i] = s * q[i];
-    g[i] = s * u[i] + (T)((double)f[i] - d);
+    g[i] = s * u[i] + (f[i] - dT);
   }
 }
 
@@ -99,9 +121,19 @@ __global__ void k_gap(const T* __restrict__ u, const T* __restrict__ f, T* __res
   if (st->done || !st->refresh) return;
   const T s = (T)st->scale;
   const double d = st->d;
-  GRID_STRIDE(i, n) {
-    g[i] = s * u[i] + (T)((double)f[i] - d);
-    p[i] = s * p[i];
+  const T dT = (T)d;
+  VEC_LOOP(i4, n) {
+    T uv[4], fv[4], pv[4], gv[4];
+    ld4(u, i4, uv);
+    ld4(f, i4, fv);
+    ld4(p, i4, pv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      gv[e] = s * uv[e] + (fv[e] - dT);
+      pv[e] = s * pv[e];
+    }
+    st4(g, i4, gv);
+    st4(p, i4, pv);
   }
 }
 
@@ -112,29 +144,39 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
                            unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   const double s = st->scale, d = st->d;
+  const T dT = (T)d;
   const bool apply = (!st->refresh) && (s != 1.0);
   const T sT = (T)s, s1 = (T)(s - 1.0);
-  Acc<T> ag, agg, auu;
+  Acc<T> ag, agg, auu, ap;
   double cnt = 0.0;
-  GRID_STRIDE(i, n) {
-    T pi = p[i], gi = g[i];
-    const T fi = f[i];
+  VEC_LOOP(i4, n) {
+    T pv[4], gv[4], fv[4];
+    ld4(p, i4, pv);
+    ld4(g, i4, gv);
+    ld4(f, i4, fv);
     if (apply) {
-      pi = sT * pi;
-      gi = sT * gi + s1 * (T)(d - (double)fi);
-      p[i] = pi;
-      g[i] = gi;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        pv[e] = sT * pv[e];
+        gv[e] = sT * gv[e] + s1 * (dT - fv[e]);
+      }
+      st4(p, i4, pv);
+      st4(g, i4, gv);
     }
-    if (pi > (T)0) {
-      const T ui = gi - (T)((double)fi - d);
-      ag.add(gi);
-      agg.add(gi * gi);
-      auu.add(ui * ui);
-      cnt += 1.0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (pv[e] > (T)0) {
+        const T ui = gv[e] - (fv[e] - dT);
+        ag.add(gv[e]);
+        agg.add(gv[e] * gv[e]);
+        auu.add(ui * ui);
+        ap.add(pv[e]);
+        cnt += 1.0;
+      }
     }
   }
-  double v[4] = {ag.value(), cnt, agg.value(), auu.value()}, tot[4];
-  if (grid_reduce<4>(v, partials, ticket, tot)) {
+  double v[5] = {ag.value(), cnt, agg.value(), auu.value(), ap.value()}, tot[5];
+  if (grid_reduce<5>(v, partials, ticket, tot)) {
     st->scale = 1.0;
     st->refresh = 0;
     st->n_c = (int)tot[1];
@@ -143,7 +185,10 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
       st->res = 0.0;
       return;
     }
-    const double gbar = (st->control == BEM_CTRL_FORCE) ? tot[0] / tot[1] : 0.0;
+    // the shift is applied to the stored gaps in the path precision; d moves by exactly that value
+    const double gbar = (st->control == BEM_CTRL_FORCE) ? (double)(T)(tot[0] / tot[1]) : 0.0;
+    st->uscale = sqrt(tot[3] / tot[1]);
+    st->pscale = tot[4] / tot[1];
     const double G = (st->control == BEM_CTRL_FORCE) ? fmax(tot[2] - tot[1] * gbar * gbar, 0.0) : tot[2];
     st->gbar = gbar;
     st->G = G;
@@ -173,13 +218,18 @@ __global__ void k_pk_dir(const T* __restrict__ p, T* __restrict__ g, T* __restri
   if (st->done) return;
   const T gbar = (T)st->gbar, beta = (T)st->beta;
   const bool shift = st->gbar != 0.0;
-  GRID_STRIDE(i, n) {
-    T gi = g[i];
-    if (shift) {
-      gi -= gbar;
-      g[i] = gi;
+  VEC_LOOP(i4, n) {
+    T pv[4], gv[4], tv[4];
+    ld4(p, i4, pv);
+    ld4(g, i4, gv);
+    ld4(t, i4, tv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (shift) gv[e] -= gbar;
+      tv[e] = (pv[e] > (T)0) ? gv[e] + beta * tv[e] : (T)0;
     }
-    t[i] = (p[i] > (T)0) ? gi + beta * t[i] : (T)0;
+    if (shift) st4(g, i4, gv);
+    st4(t, i4, tv);
   }
 }
 
@@ -189,13 +239,20 @@ __global__ void k_pk_rt(const T* __restrict__ p, const T* __restrict__ g, const 
                         const T* __restrict__ r, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   Acc<T> art, ar, at, agt;
-  GRID_STRIDE(i, n) {
-    if (p[i] > (T)0) {
-      const T ti = t[i], ri = r[i];
-      art.add(ri * ti);
-      ar.add(ri);
-      at.add(ti);
-      agt.add(g[i] * ti);
+  VEC_LOOP(i4, n) {
+    T pv[4], gv[4], tv[4], rv[4];
+    ld4(p, i4, pv);
+    ld4(g, i4, gv);
+    ld4(t, i4, tv);
+    ld4(r, i4, rv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (pv[e] > (T)0) {
+        art.add(rv[e] * tv[e]);
+        ar.add(rv[e]);
+        at.add(tv[e]);
+        agt.add(gv[e] * tv[e]);
+      }
     }
   }
   double v[4] = {art.value(), ar.value(), at.value(), agt.value()}, tot[4];
@@ -219,26 +276,41 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
                             double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   const T tau = (T)st->tau;
+  // Rounding-noise thresholds (float path only): a re-activation needs a gap below
+  // -noise * rms(u) and a projection counts as a change of the contact set only when
+  // the pressure went below -noise * mean(p).  In double both thresholds are 0.
+  const T noise = sizeof(T) == 4 ? (T)(16.0 * 1.1920929e-7) : (T)0;
+  const T gthr = -noise * (T)st->uscale, pthr = -noise * (T)st->pscale;
   Acc<T> asum;
   double nneg = 0.0, nol = 0.0;
-  GRID_STRIDE(i, n) {
-    const T pi = p[i], gi = g[i];
-    T pn;
-    if (pi > (T)0) {
-      pn = pi - tau * t[i];
-      if (pn < (T)0) {
+  VEC_LOOP(i4, n) {
+    T pv[4], gv[4], tv[4], rv[4];
+    ld4(p, i4, pv);
+    ld4(g, i4, gv);
+    ld4(t, i4, tv);
+    ld4(r, i4, rv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const T pi = pv[e], gi = gv[e];
+      T pn;
+      if (pi > (T)0) {
+        pn = pi - tau * tv[e];
+        if (pn < (T)0) {
+          if (pn < pthr) nneg += 1.0;
+          pn = (T)0;
+        }
+      } else if (gi < gthr) {
+        pn = -tau * gi;
+        nol += 1.0;
+      } else {
         pn = (T)0;
-        nneg += 1.0;
       }
-    } else if (gi < (T)0) {
-      pn = -tau * gi;
-      nol += 1.0;
-    } else {
-      pn = (T)0;
+      pv[e] = pn;
+      gv[e] = gi - tau * rv[e];
+      asum.add(pn);
     }
-    p[i] = pn;
-    g[i] = gi - tau * r[i];
-    asum.add(pn);
+    st4(p, i4, pv);
+    st4(g, i4, gv);
   }
   double v[3] = {asum.value(), nneg, nol}, tot[3];
   if (grid_reduce<3>(v, partials, ticket, tot)) {
@@ -265,6 +337,7 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
 template <typename T>
 __global__ void k_final_stats(const T* __restrict__ p, const T* __restrict__ u, const T* __restrict__ f,
                               double* partials, unsigned int* ticket, double d, double* out, size_t n) {
+  const T dT = (T)d;
   Acc<T> ag, agg, auu, ap;
   double cnt = 0.0;
   GRID_STRIDE(i, n) {
@@ -272,7 +345,7 @@ __global__ void k_final_stats(const T* __restrict__ p, const T* __restrict__ u, 
     ap.add(pi);
     if (pi != (T)0) {
       const T ui = u[i];
-      const T gi = ui + (T)((double)f[i] - d);
+      const T gi = ui + (f[i] - dT);
       ag.add(gi);
       agg.add(gi * gi);
       auu.add(ui * ui);
@@ -299,11 +372,12 @@ __global__ void k_lin_init(const T* __restrict__ u, const T* __restrict__ f, con
                            T* __restrict__ r, T* __restrict__ s, double* partials, unsigned int* ticket,
                            SolveState* st, size_t n) {
   const double d = st->d;
+  const T dT = (T)d;
   Acc<T> arr, abb;
   GRID_STRIDE(i, n) {
     T ri = (T)0;
     if (C[i]) {
-      const T bi = (T)(d - (double)f[i]);
+      const T bi = (dT - f[i]);
       ri = bi - u[i];
       arr.add(ri * ri);
       abb.add(bi * bi);
@@ -397,6 +471,7 @@ __global__ void k_detach(T* __restrict__ x, const T* __restrict__ u, const T* __
   const int N = 1 << logN;
   const size_t n = (size_t)N * N;
   const double d = st->d, sc = st->sig_c;
+  const T dT = (T)d;
   double nadd = 0.0, ndet = 0.0, ncon = 0.0;
   uint64_t hsh = 0;
   Acc<T> ap;
@@ -405,7 +480,7 @@ __global__ void k_detach(T* __restrict__ x, const T* __restrict__ u, const T* __
     const bool in = C[i] != 0;
     bool out_in = in;
     if (!in) {
-      const T gi = u[i] + (T)((double)f[i] - d);
+      const T gi = u[i] + (f[i] - dT);
       if (gi < (T)0) {
         out_in = true;
         nadd += 1.0;
@@ -483,7 +558,7 @@ Ctx ctx_of(const bem_kernel_s* k) {
   Ctx c;
   c.n = (size_t)k->N * k->N;
   c.rb = red_blocks(c.n);
-  c.eb = (int)std::min<size_t>((c.n + NTHREADS - 1) / NTHREADS, 152 * 16);
+  c.eb = (int)std::min<size_t>((c.n / 4 + NTHREADS - 1) / NTHREADS, 152 * 8);
   return c;
 }
 
