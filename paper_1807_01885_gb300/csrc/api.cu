@@ -203,7 +203,7 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
     return fail(e, "cudaMalloc(twc)");
   if ((e = cudaMalloc(&w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
   if ((e = cudaMalloc((void**)&w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
-  if ((e = cudaMalloc((void**)&w.partials, 8 * 1024 * sizeof(double))) != cudaSuccess)
+  if ((e = cudaMalloc((void**)&w.partials, 16 * 2048 * sizeof(double))) != cudaSuccess)
     return fail(e, "cudaMalloc(partials)");
   if ((e = cudaMalloc((void**)&w.ticket, sizeof(unsigned int))) != cudaSuccess) return fail(e, "cudaMalloc(ticket)");
   if ((e = cudaMalloc((void**)&w.state, sizeof(SolveState))) != cudaSuccess) return fail(e, "cudaMalloc(state)");

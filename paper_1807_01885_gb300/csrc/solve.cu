@@ -39,7 +39,9 @@ DV<T> dv(const bem_kernel_s* k) {
 }
 
 int red_blocks(size_t n) {
+  // two blocks per SM: the last block then adds few partials
   size_t b = (n + NTHREADS * 16 - 1) / (NTHREADS * 16);
+  if (b > 2 * 152) b = 2 * 152;
   b = std::max<size_t>(1, std::min<size_t>(b, RED_MAX_BLOCKS));
   return (int)b;
 }
@@ -95,7 +97,8 @@ __global__ void k_init_scale(const T* __restrict__ f, const T* __restrict__ q, c
     a0.add(qi * (d - f[i]));
     a1.add(qi * u[i]);
   }
-  double v[2] = {a0.value(), a1.value()}, tot[2];
+  Acc<T> v[2] = {a0, a1};
+  double tot[2];
   if (grid_reduce<2>(v, partials, ticket, tot)) {
     st->scale = (tot[1] > 0.0) ? tot[0] / tot[1] : 0.0;
   }
@@ -147,8 +150,7 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
   const T dT = (T)d;
   const bool apply = (!st->refresh) && (s != 1.0);
   const T sT = (T)s, s1 = (T)(s - 1.0);
-  Acc<T> ag, agg, auu, ap;
-  double cnt = 0.0;
+  Acc<T> ag, agg, auu, ap, cnt;
   VEC_LOOP(i4, n) {
     T pv[4], gv[4], fv[4];
     ld4(p, i4, pv);
@@ -171,11 +173,12 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
         agg.add(gv[e] * gv[e]);
         auu.add(ui * ui);
         ap.add(pv[e]);
-        cnt += 1.0;
+        cnt.add((T)1);
       }
     }
   }
-  double v[5] = {ag.value(), cnt, agg.value(), auu.value(), ap.value()}, tot[5];
+  Acc<T> v[5] = {ag, cnt, agg, auu, ap};
+  double tot[5];
   if (grid_reduce<5>(v, partials, ticket, tot)) {
     st->scale = 1.0;
     st->refresh = 0;
@@ -255,7 +258,8 @@ __global__ void k_pk_rt(const T* __restrict__ p, const T* __restrict__ g, const 
       }
     }
   }
-  double v[4] = {art.value(), ar.value(), at.value(), agt.value()}, tot[4];
+  Acc<T> v[4] = {art, ar, at, agt};
+  double tot[4];
   if (grid_reduce<4>(v, partials, ticket, tot)) {
     const double rbar = (st->control == BEM_CTRL_FORCE) ? tot[1] / (double)st->n_c : 0.0;
     const double den = tot[0] - rbar * tot[2];
@@ -281,8 +285,7 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
   // the pressure went below -noise * mean(p).  In double both thresholds are 0.
   const T noise = sizeof(T) == 4 ? (T)(16.0 * 1.1920929e-7) : (T)0;
   const T gthr = -noise * (T)st->uscale, pthr = -noise * (T)st->pscale;
-  Acc<T> asum;
-  double nneg = 0.0, nol = 0.0;
+  Acc<T> asum, nneg, nol;
   VEC_LOOP(i4, n) {
     T pv[4], gv[4], tv[4], rv[4];
     ld4(p, i4, pv);
@@ -296,12 +299,12 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
       if (pi > (T)0) {
         pn = pi - tau * tv[e];
         if (pn < (T)0) {
-          if (pn < pthr) nneg += 1.0;
+          if (pn < pthr) nneg.add((T)1);
           pn = (T)0;
         }
       } else if (gi < gthr) {
         pn = -tau * gi;
-        nol += 1.0;
+        nol.add((T)1);
       } else {
         pn = (T)0;
       }
@@ -312,7 +315,8 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
     st4(p, i4, pv);
     st4(g, i4, gv);
   }
-  double v[3] = {asum.value(), nneg, nol}, tot[3];
+  Acc<T> v[3] = {asum, nneg, nol};
+  double tot[3];
   if (grid_reduce<3>(v, partials, ticket, tot)) {
     st->sum_p = tot[0];
     st->n_neg = (int)tot[1];
@@ -338,8 +342,7 @@ template <typename T>
 __global__ void k_final_stats(const T* __restrict__ p, const T* __restrict__ u, const T* __restrict__ f,
                               double* partials, unsigned int* ticket, double d, double* out, size_t n) {
   const T dT = (T)d;
-  Acc<T> ag, agg, auu, ap;
-  double cnt = 0.0;
+  Acc<T> ag, agg, auu, ap, cnt;
   GRID_STRIDE(i, n) {
     const T pi = p[i];
     ap.add(pi);
@@ -349,10 +352,11 @@ __global__ void k_final_stats(const T* __restrict__ p, const T* __restrict__ u, 
       ag.add(gi);
       agg.add(gi * gi);
       auu.add(ui * ui);
-      cnt += 1.0;
+      cnt.add((T)1);
     }
   }
-  double v[5] = {ag.value(), agg.value(), auu.value(), cnt, ap.value()}, tot[5];
+  Acc<T> v[5] = {ag, agg, auu, cnt, ap};
+  double tot[5];
   if (grid_reduce<5>(v, partials, ticket, tot)) {
     for (int s = 0; s < 5; ++s) out[s] = tot[s];
   }
@@ -385,7 +389,8 @@ __global__ void k_lin_init(const T* __restrict__ u, const T* __restrict__ f, con
     r[i] = ri;
     s[i] = ri;
   }
-  double v[2] = {arr.value(), abb.value()}, tot[2];
+  Acc<T> v[2] = {arr, abb};
+  double tot[2];
   if (grid_reduce<2>(v, partials, ticket, tot)) {
     st->rr = tot[0];
     st->b2 = tot[1];
@@ -402,7 +407,8 @@ __global__ void k_lin_alpha(const T* __restrict__ s, const T* __restrict__ q, co
   if (st->done) return;
   Acc<T> a;
   GRID_STRIDE(i, n) if (C[i]) a.add(s[i] * q[i]);
-  double v[1] = {a.value()}, tot[1];
+  Acc<T> v[1] = {a};
+  double tot[1];
   if (grid_reduce<1>(v, partials, ticket, tot)) {
     const double alpha = st->rr / tot[0];
     if (!(tot[0] > 0.0) || !isfinite(alpha)) {
@@ -428,7 +434,8 @@ __global__ void k_lin_update(T* __restrict__ x, T* __restrict__ r, const T* __re
       arr.add(ri * ri);
     }
   }
-  double v[1] = {arr.value()}, tot[1];
+  Acc<T> v[1] = {arr};
+  double tot[1];
   if (grid_reduce<1>(v, partials, ticket, tot)) {
     st->beta = tot[0] / st->rr;
     st->rr = tot[0];
@@ -472,9 +479,7 @@ __global__ void k_detach(T* __restrict__ x, const T* __restrict__ u, const T* __
   const size_t n = (size_t)N * N;
   const double d = st->d, sc = st->sig_c;
   const T dT = (T)d;
-  double nadd = 0.0, ndet = 0.0, ncon = 0.0;
-  uint64_t hsh = 0;
-  Acc<T> ap;
+  Acc<T> nadd, ndet, ncon, ap, hq[4];
   GRID_STRIDE(i, n) {
     const int r = (int)(i >> logN), c = (int)(i & (N - 1));
     const bool in = C[i] != 0;
@@ -483,34 +488,38 @@ __global__ void k_detach(T* __restrict__ x, const T* __restrict__ u, const T* __
       const T gi = u[i] + (f[i] - dT);
       if (gi < (T)0) {
         out_in = true;
-        nadd += 1.0;
+        nadd.add((T)1);
       }
     } else {
       const bool inner = (r > 0 && C[i - N]) && (r < N - 1 && C[i + N]) && (c > 0 && C[i - 1]) &&
                          (c < N - 1 && C[i + 1]);
       if (!inner && -(double)x[i] > sc) {
         out_in = false;
-        ndet += 1.0;
+        ndet.add((T)1);
       }
     }
     Cn[i] = out_in ? 1 : 0;
     if (!out_in) x[i] = (T)0;
     if (out_in) {
-      ncon += 1.0;
-      hsh += mix64((uint64_t)i);
+      ncon.add((T)1);
       ap.add(x[i]);
+      // order-free set hash: the sum of a 64-bit mix of the member indices, carried as
+      // four exact sums of 16-bit digits
+      const uint64_t h = mix64((uint64_t)i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) hq[k].add((T)(double)((h >> (16 * k)) & 0xffffu));
     }
   }
-  // hash: sum of mixed indices (order-free), carried as two exact 32-bit halves in double
-  double v[6] = {nadd, ndet, ncon, ap.value(), (double)(uint32_t)(hsh & 0xffffffffu), (double)(uint32_t)(hsh >> 32)};
-  double tot[6];
-  if (grid_reduce<6>(v, partials, ticket, tot)) {
+  Acc<T> v[8] = {nadd, ndet, ncon, ap, hq[0], hq[1], hq[2], hq[3]};
+  double tot[8];
+  if (grid_reduce<8>(v, partials, ticket, tot)) {
     st->n_add = (int)tot[0];
     st->n_detach = (int)tot[1];
     st->n_c = (int)tot[2];
     st->sum_p = tot[3];
-    const uint64_t lo = (uint64_t)tot[4], hi = (uint64_t)tot[5];
-    st->mask_hash = lo + (hi << 32);
+    uint64_t hsh = 0;
+    for (int k = 0; k < 4; ++k) hsh += ((uint64_t)tot[4 + k]) << (16 * k);
+    st->mask_hash = hsh;
   }
 }
 
@@ -532,7 +541,8 @@ __global__ void k_init_clamp(T* __restrict__ p, double* partials, unsigned int* 
     p[i] = v;
     a.add(v);
   }
-  double v[1] = {a.value()}, tot[1];
+  Acc<T> v[1] = {a};
+  double tot[1];
   if (grid_reduce<1>(v, partials, ticket, tot)) {
     if (st->control == BEM_CTRL_FORCE) {
       if (tot[0] > 0.0) st->scale = st->target / (st->delta2 * tot[0]);
@@ -567,7 +577,7 @@ bem_status final_stats(bem_kernel_s* k, const T* p, double d, double* out5, cuda
   const Ctx c = ctx_of<T>(k);
   DV<T> v = dv<T>(k);
   launch_matvec<T>(k, p, v.u, s, nullptr);
-  double* dout = k->ws.partials + 7 * RED_MAX_BLOCKS;
+  double* dout = k->ws.partials + 12 * RED_MAX_BLOCKS;
   k_final_stats<T><<<c.rb, NTHREADS, 0, s>>>(p, v.u, v.f, k->ws.partials, k->ws.ticket, d, dout, c.n);
   note_launches(1);
   BEM_CUDA_TRY(cudaGetLastError());
@@ -747,12 +757,13 @@ bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit
 template <typename T>
 __global__ void k_nonfinite(const T* __restrict__ a, const T* __restrict__ b, double* partials, unsigned int* ticket,
                             double* out, size_t n) {
-  double cnt = 0.0;
+  Acc<T> cnt;
   GRID_STRIDE(i, n) {
-    if (!isfinite((double)a[i])) cnt += 1.0;
-    if (b != nullptr && !isfinite((double)b[i])) cnt += 1.0;
+    if (!isfinite(a[i])) cnt.add((T)1);
+    if (b != nullptr && !isfinite(b[i])) cnt.add((T)1);
   }
-  double v[1] = {cnt}, tot[1];
+  Acc<T> v[1] = {cnt};
+  double tot[1];
   if (grid_reduce<1>(v, partials, ticket, tot)) out[0] = tot[0];
 }
 
@@ -766,7 +777,7 @@ bem_status solve_typed(bem_kernel_s* k, const bem_problem* prob, const T* f, con
   *res = bem_result{};
   {
     const Ctx c = ctx_of<T>(k);
-    double* dout = k->ws.partials + 7 * RED_MAX_BLOCKS;
+    double* dout = k->ws.partials + 12 * RED_MAX_BLOCKS;
     double bad = 0.0;
     k_nonfinite<T><<<c.rb, NTHREADS, 0, s>>>(v.f, pinit, k->ws.partials, k->ws.ticket, dout, n);
     note_launches(1);
