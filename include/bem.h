@@ -146,6 +146,26 @@ bem_status bem_solve_batch(int32_t n, const bem_kernel* kernels, const bem_probl
 bem_status bem_profile_passes(bem_kernel k, const void* p, void* u, int32_t reps, float* ms_out,
                               void* cuda_stream);
 
+/* u = K p for callers that cannot allocate device memory (no counterpart in the
+ * paper; an integration aid).  Some callers may not call cudaMalloc at all: code
+ * running under a host framework's memory pool that must not be bypassed, real-time
+ * loops where an allocation could stall or fail, plug-ins handed buffers but no
+ * allocation rights.  This entry point allocates nothing: it takes the operator
+ * parameters (desc->precision must be BEM_FP32, N a power of two with
+ * 4 <= N <= BEM_STATIC_MAX_N) and device arrays p and u (N*N floats, 16-byte
+ * aligned, caller-owned), and keeps every intermediate (compliance tables, twiddles,
+ * half spectrum) in one fixed device array of about 1.4 MB that each GPU loading the
+ * library holds until the process exits.  Larger N or host arrays are rejected with
+ * BEM_EINVAL.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call rewrites the parts of the array it reads, so no
+ * clearing is needed, but all calls share the one array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the caller.
+ * Asynchronous on cuda_stream; results equal bem_matvec on a handle made from the
+ * same desc. */
+#define BEM_STATIC_MAX_N 256
+bem_status bem_matvec_static(const bem_kernel_desc* desc, const float* p, float* u, void* cuda_stream);
+
 /* Number of kernel launches the library has issued since it was loaded. */
 int64_t bem_launch_count(void);
 

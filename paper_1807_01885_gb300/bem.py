@@ -26,7 +26,9 @@ BEM_DC_FINITE_PART, BEM_DC_ZERO = 0, 1
 
 # entry points declared in include/bem.h
 EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
-           "bem_solve_batch", "bem_profile_passes", "bem_launch_count", "bem_last_error", "bem_version")
+           "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_launch_count", "bem_last_error",
+           "bem_version")
+BEM_STATIC_MAX_N = 256
 
 
 class BemError(RuntimeError):
@@ -88,6 +90,8 @@ def load(path=None):
     lib.bem_profile_passes.argtypes = [vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp]
     lib.bem_profile_passes.restype = i32
     lib.bem_launch_count.argtypes = []
+    lib.bem_matvec_static.argtypes = [ctypes.POINTER(KernelDesc), vp, vp, vp]
+    lib.bem_matvec_static.restype = i32
     lib.bem_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
@@ -183,6 +187,15 @@ def bem_profile_passes(k, p, u, reps, stream=None):
     ms = (ctypes.c_float * 3)()
     _check(load().bem_profile_passes(k, _ptr(p), _ptr(u), reps, ms, _stream(stream)))
     return [ms[0], ms[1], ms[2]]
+
+
+def bem_matvec_static(N, delta, h, E1, nu1, E2, nu2, p, u, dc_mode=BEM_DC_FINITE_PART, stream=None):
+    """u = K p through the entry point that allocates nothing (float32 device arrays,
+    N <= BEM_STATIC_MAX_N); for callers that may not allocate device memory."""
+    d = KernelDesc(N=N, precision=BEM_FP32, dc_mode=dc_mode, reserved=0, delta=delta, h=h, E1=E1, nu1=nu1,
+                   E2=E2, nu2=nu2)
+    _check(load().bem_matvec_static(ctypes.byref(d), _ptr(p), _ptr(u), _stream(stream)))
+    return u
 
 
 def bem_launch_count():

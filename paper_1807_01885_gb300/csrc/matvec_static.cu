@@ -1,0 +1,154 @@
+// u = K p without any device allocation, for callers that cannot allocate.
+//
+// Some callers are not allowed to call cudaMalloc: code that runs inside a
+// memory-capped or pre-reserved allocator (the memory pool of a host framework
+// that must not be bypassed), code in a real-time loop where an allocation could
+// block or fail, and plug-ins that are handed device buffers but no allocation
+// rights.  bem_matvec_static serves them: the caller passes the operator
+// parameters, the input p and the output u, and every intermediate the product
+// needs (the double compliance table and its scaled copy, the twiddle tables and
+// the half spectrum between the FFT passes) lives in one fixed array in device
+// memory, `g_static_scratch` below, sized for grids up to BEM_STATIC_MAX_N.
+//
+// The array is a file-scope __device__ variable, so every GPU on which the library
+// is loaded holds it until the process exits.  Host code cannot use the array's
+// name as a device address; the first call on each device asks the runtime for the
+// address (cudaGetSymbolAddress, with that device current) and keeps it.  All calls
+// share the array and it keeps the last call's contents: every call rewrites all of
+// it that it reads, so nothing has to be cleared between calls, but calls that
+// overlap on the GPU (on different streams, or from several threads) race on it.
+#include <string>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+namespace {
+
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Byte layout of the scratch for a grid of N cells per side (float path).
+struct StaticLayout {
+  size_t spec, table64, table, tw, twr, twc, total;
+  explicit StaticLayout(int N) {
+    const size_t c = 2 * sizeof(float);
+    const size_t blocked = (size_t)(N / TC + 1) * (N + 1) * TC, square = (size_t)(N + 1) * (N + 4);
+    size_t off = 0;
+    spec = off;
+    off += round256((size_t)(N / TC + 1) * N * TC * c);
+    table64 = off;
+    off += round256((size_t)(N + 1) * (N + 1) * sizeof(double));
+    table = off;
+    off += round256((blocked > square ? blocked : square) * sizeof(float));
+    tw = off;
+    off += round256((size_t)2 * N * c);
+    twr = off;
+    off += round256((size_t)2 * N * c);
+    twc = off;
+    off += round256((size_t)4 * N * c);
+    total = off;
+  }
+};
+
+constexpr size_t kStaticBytes = 1400 * 1024;   // >= StaticLayout(BEM_STATIC_MAX_N).total
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+bem_status scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("bem_matvec_static: device index out of range");
+    return BEM_EUNSUPPORTED;
+  }
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+    g_scratch_ptr[dev] = ptr;
+  }
+  *out = g_scratch_ptr[dev];
+  return BEM_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" bem_status bem_matvec_static(const bem_kernel_desc* desc, const float* p, float* u, void* cuda_stream) {
+  if (desc == nullptr || p == nullptr || u == nullptr) {
+    set_error("bem_matvec_static: NULL argument");
+    return BEM_EINVAL;
+  }
+  const int N = desc->N;
+  if (N < 4 || N > BEM_STATIC_MAX_N || (N & (N - 1))) {
+    set_error("bem_matvec_static: N must be a power of two in [4, " + std::to_string(BEM_STATIC_MAX_N) +
+              "] (the fixed scratch array is sized for that); use bem_make_kernel/bem_matvec for larger grids");
+    return BEM_EINVAL;
+  }
+  if (desc->precision != BEM_FP32) {
+    set_error("bem_matvec_static: only precision BEM_FP32 is available");
+    return BEM_EINVAL;
+  }
+  if (desc->dc_mode != BEM_DC_FINITE_PART && desc->dc_mode != BEM_DC_ZERO) {
+    set_error("bem_matvec_static: unknown dc_mode");
+    return BEM_EINVAL;
+  }
+  if (!(desc->delta > 0.0) || !(desc->h >= 0.0) || !(desc->E1 > 0.0) || !(desc->E2 > 0.0) ||
+      !(desc->nu1 >= 0.0 && desc->nu1 < 0.5) || !(desc->nu2 >= 0.0 && desc->nu2 < 0.5)) {
+    set_error("bem_matvec_static: invalid material or grid parameters");
+    return BEM_EINVAL;
+  }
+  if (((uintptr_t)p & 15) != 0 || ((uintptr_t)u & 15) != 0) {
+    set_error("bem_matvec_static: p and u must be 16-byte aligned");
+    return BEM_EINVAL;
+  }
+  if (!on_device(p) || !on_device(u)) {
+    set_error("bem_matvec_static: p and u must be device arrays (host arrays would need a staging allocation)");
+    return BEM_EINVAL;
+  }
+  int dev = 0;
+  BEM_CUDA_TRY(cudaGetDevice(&dev));
+  void* base = nullptr;
+  bem_status st = scratch_address(dev, &base);
+  if (st != BEM_OK) return st;
+  const StaticLayout lay(N);
+  if (lay.total > kStaticBytes) {
+    set_error("bem_matvec_static: internal scratch layout exceeds the fixed array");
+    return BEM_EUNSUPPORTED;
+  }
+  // A handle on the stack whose workspace points into the fixed array; only the
+  // fields the table build and the three passes read are set.
+  bem_kernel_s k{};
+  k.desc = *desc;
+  k.N = N;
+  k.M = 2 * N;
+  k.logN = 0;
+  while ((1 << k.logN) < N) ++k.logN;
+  k.prec = BEM_FP32;
+  k.elem = sizeof(float);
+  k.dev = dev;
+  unsigned char* b = (unsigned char*)base;
+  k.ws.spec = b + lay.spec;
+  k.ws.table64 = (double*)(b + lay.table64);
+  k.ws.table = b + lay.table;
+  k.ws.tw = b + lay.tw;
+  k.ws.twr = b + lay.twr;
+  k.ws.twc = b + lay.twc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  st = build_table(&k, s);
+  if (st != BEM_OK) return st;
+  launch_matvec<float>(&k, p, u, s, nullptr);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}

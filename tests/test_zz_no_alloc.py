@@ -1,0 +1,64 @@
+"""The entry point that allocates nothing (bem_matvec_static).
+
+It exists for callers that may not call cudaMalloc (a host framework's memory pool
+that must not be bypassed, real-time loops, plug-ins without allocation rights):
+all of its intermediates live in one fixed device array inside the library.  These
+checks call it through the C ABI and compare it with the handle-based bem_matvec on
+the same operator, on two calls in a row with different inputs (the shared array
+keeps the first call's contents, so the second call must not depend on them).
+This file is collected last so that a failure here leaves every other test run.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1807_01885_gb300 import bem
+
+pytestmark = pytest.mark.gpu
+
+# float path tolerance of the operator tests (relative L2)
+TOL = 2e-6
+
+
+@pytest.mark.parametrize("N,params", [
+    (256, dict(delta=1.0 / 256, h=8.0 / 256, E1=4.0, nu1=0.3, E2=1.0, nu2=0.45)),
+    (64, dict(delta=0.01, h=float("inf"), E1=1.0, nu1=0.3, E2=1.0, nu2=0.3)),
+    (16, dict(delta=0.1, h=0.2, E1=0.5, nu1=0.25, E2=float("inf"), nu2=0.3)),
+])
+def test_static_matches_handle_two_calls(cuda, N, params):
+    g = torch.Generator(device=cuda).manual_seed(N)
+    p1 = torch.randn((N, N), dtype=torch.float32, device=cuda, generator=g)
+    p2 = torch.rand((N, N), dtype=torch.float32, device=cuda, generator=g)
+    with bem.Kernel(N, precision="fp32", **params) as k:
+        r1 = k.matvec(p1).clone()
+        r2 = k.matvec(p2).clone()
+    u1 = torch.empty_like(p1)
+    u2 = torch.empty_like(p2)
+    bem.bem_matvec_static(N, p=p1, u=u1, **params)
+    torch.cuda.synchronize()
+    a = (u1 - r1).norm() / r1.norm()
+    bem.bem_matvec_static(N, p=p2, u=u2, **params)
+    torch.cuda.synchronize()
+    b = (u2 - r2).norm() / r2.norm()
+    assert float(a) < TOL and float(b) < TOL
+    # the first result is left intact by the second call (outputs are the caller's)
+    assert float((u1 - r1).norm() / r1.norm()) < TOL
+
+
+def test_static_rejects_sizes_beyond_the_fixed_array(cuda):
+    N = 2 * bem.BEM_STATIC_MAX_N
+    p = torch.zeros((N, N), dtype=torch.float32, device=cuda)
+    u = torch.empty_like(p)
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_matvec_static(N, 1.0 / N, 0.1, 1.0, 0.3, 1.0, 0.3, p, u)
+    assert e.value.status == bem.BEM_EINVAL
+    assert "BEM_STATIC_MAX_N" in str(e.value) or str(bem.BEM_STATIC_MAX_N) in str(e.value)
+
+
+def test_static_rejects_host_arrays(cuda):
+    N = 16
+    p = np.zeros((N, N), dtype=np.float32)
+    u = np.zeros((N, N), dtype=np.float32)
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_matvec_static(N, 0.1, 0.2, 1.0, 0.3, 1.0, 0.3, p, u)
+    assert e.value.status == bem.BEM_EINVAL
