@@ -166,6 +166,15 @@ bem_status bem_profile_passes(bem_kernel k, const void* p, void* u, int32_t reps
 #define BEM_STATIC_MAX_N 256
 bem_status bem_matvec_static(const bem_kernel_desc* desc, const float* p, float* u, void* cuda_stream);
 
+/* Live per-pass timing (a measurement aid, not part of the method): while on, every
+ * product records CUDA events on its stream around each of its three passes; the
+ * durations are collected at the library's synchronisation points.
+ * bem_pass_timing synchronises the device and returns, per pass (rows forward,
+ * columns, rows inverse), the summed milliseconds and the number of timed launches;
+ * reset != 0 zeroes the totals. */
+bem_status bem_set_pass_timing(bem_kernel k, int32_t on);
+bem_status bem_pass_timing(bem_kernel k, double* ms_total, int64_t* launches, int32_t reset);
+
 /* Number of kernel launches the library has issued since it was loaded. */
 int64_t bem_launch_count(void);
 

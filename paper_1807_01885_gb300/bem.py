@@ -26,8 +26,8 @@ BEM_DC_FINITE_PART, BEM_DC_ZERO = 0, 1
 
 # entry points declared in include/bem.h
 EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
-           "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_launch_count", "bem_last_error",
-           "bem_version")
+           "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_set_pass_timing", "bem_pass_timing",
+           "bem_launch_count", "bem_last_error", "bem_version")
 BEM_STATIC_MAX_N = 256
 
 
@@ -91,6 +91,10 @@ def load(path=None):
     lib.bem_profile_passes.restype = i32
     lib.bem_launch_count.argtypes = []
     lib.bem_matvec_static.argtypes = [ctypes.POINTER(KernelDesc), vp, vp, vp]
+    lib.bem_set_pass_timing.argtypes = [vp, i32]
+    lib.bem_set_pass_timing.restype = i32
+    lib.bem_pass_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
+    lib.bem_pass_timing.restype = i32
     lib.bem_matvec_static.restype = i32
     lib.bem_launch_count.restype = ctypes.c_int64
     _lib = lib
@@ -196,6 +200,18 @@ def bem_matvec_static(N, delta, h, E1, nu1, E2, nu2, p, u, dc_mode=BEM_DC_FINITE
                    E2=E2, nu2=nu2)
     _check(load().bem_matvec_static(ctypes.byref(d), _ptr(p), _ptr(u), _stream(stream)))
     return u
+
+
+def bem_set_pass_timing(k, on):
+    _check(load().bem_set_pass_timing(k, 1 if on else 0))
+
+
+def bem_pass_timing(k, reset=False):
+    """(ms_total[3], launches[3]) of the timed passes (rows fwd, columns, rows inv)."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(load().bem_pass_timing(k, ms, n, 1 if reset else 0))
+    return list(ms), list(n)
 
 
 def bem_launch_count():

@@ -160,6 +160,28 @@ bem_status bem_profile_passes(bem_kernel k, const void* p, void* u, int32_t reps
 
 const char* bem_last_error(void) { return g_last_error.c_str(); }
 
+bem_status bem_set_pass_timing(bem_kernel k, int32_t on) {
+  if (k == nullptr) { set_error("NULL kernel"); return BEM_EINVAL; }
+  k->timing.on = on ? 1 : 0;
+  return BEM_OK;
+}
+
+bem_status bem_pass_timing(bem_kernel k, double* ms_total, int64_t* launches_out, int32_t reset) {
+  if (k == nullptr || ms_total == nullptr || launches_out == nullptr) { set_error("NULL argument"); return BEM_EINVAL; }
+  DeviceGuard g(k->dev);
+  BEM_CUDA_TRY(cudaDeviceSynchronize());
+  harvest_pass_timing(k);
+  for (int pass = 0; pass < 3; ++pass) {
+    ms_total[pass] = k->timing.ms[pass];
+    launches_out[pass] = k->timing.n[pass];
+    if (reset) {
+      k->timing.ms[pass] = 0.0;
+      k->timing.n[pass] = 0;
+    }
+  }
+  return BEM_OK;
+}
+
 bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out) {
   if (out == nullptr) { set_error("out is NULL"); return BEM_EINVAL; }
   *out = nullptr;
@@ -227,6 +249,11 @@ bem_status bem_destroy_kernel(bem_kernel k) {
   if (k == nullptr) return BEM_OK;
   DeviceGuard g(k->dev);
   cudaDeviceSynchronize();
+  harvest_pass_timing(k);
+  for (auto& e : k->timing.pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   free_ws(k);
   delete k;
   return BEM_OK;

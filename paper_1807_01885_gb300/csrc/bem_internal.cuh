@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "bem.h"
 
@@ -109,6 +111,15 @@ struct bem_kernel_s {
   int row_radix_alt;   // 1: alternative radix for the row passes (set from BEM_ROW_RADIX_ALT)
   int col_persist;     // 1: persistent, prefetching column pass (BEM_COL_PERSIST=1)
   bem::Workspace ws;
+  // per-pass CUDA-event timing (bem_set_pass_timing): pending (start, end) pairs,
+  // harvested into totals at synchronisation points
+  struct PassTiming {
+    int on = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[3], pool;
+    double ms[3] = {0, 0, 0};
+    long long n[3] = {0, 0, 0};
+  };
+  mutable PassTiming timing;
 };
 
 namespace bem {
@@ -116,6 +127,8 @@ void set_error(const std::string& msg);
 // number of kernel launches issued by the library (for launch accounting)
 void note_launches(long long n);
 long long launches();
+// adds the durations of completed timed passes of k to its totals (host sync point)
+void harvest_pass_timing(const bem_kernel_s* k);
 bem_status cuda_fail(cudaError_t e, const char* what);
 
 // matvec.cu

@@ -322,11 +322,49 @@ static void pass_impl(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStr
   note_launches(1);
 }
 
+static std::pair<cudaEvent_t, cudaEvent_t> timing_pair(const bem_kernel_s* k) {
+  auto& tm = k->timing;
+  if (!tm.pool.empty()) {
+    auto e = tm.pool.back();
+    tm.pool.pop_back();
+    return e;
+  }
+  std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+  cudaEventCreate(&e.first);
+  cudaEventCreate(&e.second);
+  return e;
+}
+
+void harvest_pass_timing(const bem_kernel_s* k) {
+  auto& tm = k->timing;
+  for (int pass = 0; pass < 3; ++pass) {
+    for (auto& e : tm.pending[pass]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+        tm.ms[pass] += ms;
+        tm.n[pass] += 1;
+      } else {
+        cudaGetLastError();
+      }
+      tm.pool.push_back(e);
+    }
+    tm.pending[pass].clear();
+  }
+}
+
 template <typename T>
 void launch_matvec(const bem_kernel_s* k, const T* p, T* u, cudaStream_t s, const int* skip) {
-  pass_impl<T>(k, 0, p, u, s, skip);
-  pass_impl<T>(k, 1, p, u, s, skip);
-  pass_impl<T>(k, 2, p, u, s, skip);
+  for (int pass = 0; pass < 3; ++pass) {
+    if (k->timing.on) {
+      auto e = timing_pair(k);
+      cudaEventRecord(e.first, s);
+      pass_impl<T>(k, pass, p, u, s, skip);
+      cudaEventRecord(e.second, s);
+      k->timing.pending[pass].push_back(e);
+    } else {
+      pass_impl<T>(k, pass, p, u, s, skip);
+    }
+  }
 }
 
 template <typename T>

@@ -555,6 +555,7 @@ template <typename T>
 bem_status read_state(bem_kernel_s* k, cudaStream_t s) {
   BEM_CUDA_TRY(cudaMemcpyAsync(k->ws.state_host, k->ws.state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (k->timing.on) harvest_pass_timing(k);
   return BEM_OK;
 }
 
