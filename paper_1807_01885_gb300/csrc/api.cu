@@ -5,6 +5,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <memory>
+#include <mutex>
+#include <vector>
 #include <string>
 
 #include "bem_internal.cuh"
@@ -26,6 +29,8 @@ bem_status cuda_fail(cudaError_t e, const char* what) {
 
 bem_status solve_contact_device(bem_kernel_s* k, const bem_problem* prob, const void* f, const void* pinit,
                                 uint8_t* mask, void* p_out, bem_result* res, cudaStream_t s);
+bem_status solve_batch_device(int n, bem_kernel_s* const* ks, const bem_problem* probs, const bool* has_pinit,
+                              bem_result* res, cudaStream_t const* strm);
 
 namespace {
 
@@ -58,6 +63,41 @@ bem_status check_desc(const bem_kernel_desc* d) {
   return BEM_OK;
 }
 
+bem_status check_problem(const bem_problem* prob) {
+  if (prob == nullptr || prob->height == nullptr) {
+    set_error("NULL problem or height map");
+    return BEM_EINVAL;
+  }
+  if (!(prob->tol > 0.0) || prob->max_iter <= 0 || !(prob->dgamma >= 0.0) || !isfinite(prob->target)) {
+    set_error("invalid problem (tol > 0, max_iter > 0, dgamma >= 0, finite target)");
+    return BEM_EINVAL;
+  }
+  if (prob->control != BEM_CTRL_DEPTH && prob->control != BEM_CTRL_FORCE) {
+    set_error("unknown control");
+    return BEM_EINVAL;
+  }
+  if (prob->control == BEM_CTRL_FORCE && (prob->dgamma > 0.0 || !(prob->target > 0.0))) {
+    set_error("force control needs dgamma == 0 and a positive force");
+    return BEM_EINVAL;
+  }
+  return BEM_OK;
+}
+
+// Library-owned non-blocking streams for concurrent batch instances (per device).
+constexpr int kBatchStreams = 32;
+cudaStream_t batch_stream(int dev, int i) {
+  static std::mutex mu;
+  static std::vector<std::vector<cudaStream_t>> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1);
+  auto& pool = pools[dev];
+  if (pool.empty()) {
+    pool.resize(kBatchStreams, nullptr);
+    for (auto& st : pool) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  }
+  return pool[i % kBatchStreams];
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -85,6 +125,8 @@ void free_ws(bem_kernel_s* k) {
   cudaFree(w.ticket);
   cudaFree(w.state);
   cudaFreeHost(w.state_host);
+  cudaFreeHost(w.aux_host);
+  if (w.done_ev != nullptr) cudaEventDestroy(w.done_ev);
   cudaFree(w.stage_in);
   cudaFree(w.stage_out);
   w = Workspace{};
@@ -231,6 +273,10 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
   if ((e = cudaMalloc((void**)&w.state, sizeof(SolveState))) != cudaSuccess) return fail(e, "cudaMalloc(state)");
   if ((e = cudaMallocHost((void**)&w.state_host, sizeof(SolveState))) != cudaSuccess)
     return fail(e, "cudaMallocHost(state)");
+  if ((e = cudaMallocHost((void**)&w.aux_host, 16 * sizeof(double))) != cudaSuccess)
+    return fail(e, "cudaMallocHost(aux)");
+  if ((e = cudaEventCreateWithFlags(&w.done_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e, "cudaEventCreate");
   if ((e = cudaMalloc(&w.stage_in, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_in)");
   if ((e = cudaMalloc(&w.stage_out, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_out)");
   if ((e = cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(e, "memset(ticket)");
@@ -250,6 +296,7 @@ bem_status bem_destroy_kernel(bem_kernel k) {
   DeviceGuard g(k->dev);
   cudaDeviceSynchronize();
   harvest_pass_timing(k);
+  if (k->graphs.pk_exec != nullptr) cudaGraphExecDestroy(k->graphs.pk_exec);
   for (auto& e : k->timing.pool) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -297,22 +344,12 @@ bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream) {
 
 bem_status bem_solve_contact(bem_kernel k, const bem_problem* prob, void* p_out, bem_result* res,
                              void* cuda_stream) {
-  if (k == nullptr || prob == nullptr || res == nullptr || prob->height == nullptr) {
+  if (k == nullptr || res == nullptr) {
     set_error("NULL argument");
     return BEM_EINVAL;
   }
-  if (!(prob->tol > 0.0) || prob->max_iter <= 0 || !(prob->dgamma >= 0.0) || !isfinite(prob->target)) {
-    set_error("invalid problem (tol > 0, max_iter > 0, dgamma >= 0, finite target)");
-    return BEM_EINVAL;
-  }
-  if (prob->control != BEM_CTRL_DEPTH && prob->control != BEM_CTRL_FORCE) {
-    set_error("unknown control");
-    return BEM_EINVAL;
-  }
-  if (prob->control == BEM_CTRL_FORCE && (prob->dgamma > 0.0 || !(prob->target > 0.0))) {
-    set_error("force control needs dgamma == 0 and a positive force");
-    return BEM_EINVAL;
-  }
+  bem_status pst = check_problem(prob);
+  if (pst != BEM_OK) return pst;
   DeviceGuard g(k->dev);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t n = (size_t)k->N * k->N;
@@ -357,14 +394,76 @@ bem_status bem_solve_batch(int32_t n, const bem_kernel* kernels, const bem_probl
     set_error("invalid batch arguments");
     return BEM_EINVAL;
   }
-  bem_status first = BEM_OK;
+  if (n == 0) return BEM_OK;
   for (int32_t i = 0; i < n; ++i) {
+    if (kernels[i] == nullptr) { set_error("NULL kernel in batch"); return BEM_EINVAL; }
+    bem_status pst = check_problem(&probs[i]);
+    if (pst != BEM_OK) return pst;
+    if (kernels[i]->dev != kernels[0]->dev) { set_error("batch kernels must live on one device"); return BEM_EINVAL; }
+    for (int32_t j = 0; j < i; ++j)
+      if (kernels[j] == kernels[i]) { set_error("a kernel handle appears twice in the batch"); return BEM_EINVAL; }
+  }
+  DeviceGuard g(kernels[0]->dev);
+  cudaStream_t caller = (cudaStream_t)cuda_stream;
+  cudaEvent_t ready;
+  BEM_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  BEM_CUDA_TRY(cudaEventRecord(ready, caller));
+  bem_status first = BEM_OK;
+  // non-adhesive instances run concurrently, one precision group at a time
+  for (int prec : {BEM_FP32, BEM_FP64}) {
+    std::vector<int> idx;
+    for (int32_t i = 0; i < n; ++i)
+      if (probs[i].dgamma == 0.0 && kernels[i]->prec == prec) idx.push_back(i);
+    if (idx.empty()) continue;
+    const int m = (int)idx.size();
+    std::vector<bem_kernel_s*> ks(m);
+    std::vector<bem_problem> ps(m);
+    std::vector<bem_result> rs(m);
+    std::vector<cudaStream_t> strm(m);
+    std::unique_ptr<bool[]> has_pinit(new bool[m]);
+    for (int a = 0; a < m; ++a) {
+      const int i = idx[a];
+      bem_kernel_s* k = kernels[i];
+      ks[a] = k;
+      ps[a] = probs[i];
+      strm[a] = batch_stream(k->dev, a);
+      if (a < kBatchStreams) BEM_CUDA_TRY(cudaStreamWaitEvent(strm[a], ready, 0));
+      const size_t bytes = (size_t)k->N * k->N * k->elem;
+      char* vec = (char*)k->ws.vec;
+      BEM_CUDA_TRY(cudaMemcpyAsync(vec + 5 * bytes, probs[i].height, bytes, cudaMemcpyDefault, strm[a]));
+      has_pinit[a] = probs[i].p_init != nullptr;
+      if (has_pinit[a])
+        BEM_CUDA_TRY(cudaMemcpyAsync(vec + 6 * bytes, probs[i].p_init, bytes, cudaMemcpyDefault, strm[a]));
+    }
+    bem_status st = solve_batch_device(m, ks.data(), ps.data(), has_pinit.get(), rs.data(), strm.data());
+    if (st != BEM_OK) {
+      cudaEventDestroy(ready);
+      return st;
+    }
+    for (int a = 0; a < m; ++a) {
+      const int i = idx[a];
+      res[i] = rs[a];
+      if (p_out != nullptr && p_out[i] != nullptr) {
+        bem_kernel_s* k = ks[a];
+        const size_t bytes = (size_t)k->N * k->N * k->elem;
+        BEM_CUDA_TRY(cudaMemcpyAsync(p_out[i], k->ws.vec, bytes, cudaMemcpyDefault, strm[a]));
+      }
+      if (rs[a].status != BEM_OK && first == BEM_OK) first = (bem_status)rs[a].status;
+    }
+    for (int a = 0; a < m && a < kBatchStreams; ++a) BEM_CUDA_TRY(cudaStreamSynchronize(strm[a]));
+  }
+  cudaEventDestroy(ready);
+  // adhesive steps carry host-side outer iterations: one after another on the caller's stream
+  for (int32_t i = 0; i < n; ++i) {
+    if (probs[i].dgamma == 0.0) continue;
     bem_status st = bem_solve_contact(kernels[i], &probs[i], p_out ? p_out[i] : nullptr, &res[i], cuda_stream);
     if (st != BEM_OK) {
       res[i].status = st;
       if (first == BEM_OK) first = st;
     }
   }
+  if (first == BEM_ENOCONV) set_error("an instance reached its iteration limit");
+  if (first == BEM_ENAN) set_error("an instance met a non-finite value");
   return first;
 }
 

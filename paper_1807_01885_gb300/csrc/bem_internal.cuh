@@ -95,6 +95,8 @@ struct Workspace {
   unsigned int* ticket = nullptr;
   SolveState* state = nullptr;
   SolveState* state_host = nullptr;   // pinned mirror
+  double* aux_host = nullptr;         // pinned: final sums [0..4], non-finite count [7]
+  cudaEvent_t done_ev = nullptr;      // batch rounds: state copied back
   void* stage_in = nullptr;  // staging for host arguments (N*N)
   void* stage_out = nullptr;
 };
@@ -120,6 +122,13 @@ struct bem_kernel_s {
     long long n[3] = {0, 0, 0};
   };
   mutable PassTiming timing;
+  // captured CG iteration chunk (replayed by solves on this handle)
+  struct Graphs {
+    int warm = 0;                      // one chunk ran plainly (kernel attributes are set)
+    cudaGraphExec_t pk_exec = nullptr;
+    long long pk_nodes = 0;            // kernel nodes in pk_exec (launch accounting)
+  };
+  Graphs graphs;
 };
 
 namespace bem {

@@ -573,8 +573,10 @@ Ctx ctx_of(const bem_kernel_s* k) {
   return c;
 }
 
+// Final statistics from a fresh u = K p, copied asynchronously to the handle's pinned
+// aux_host[0..4]: sums over {p != 0} of g, g^2, u^2, their count, and sum p.
 template <typename T>
-bem_status final_stats(bem_kernel_s* k, const T* p, double d, double* out5, cudaStream_t s) {
+bem_status final_stats_launch(bem_kernel_s* k, const T* p, double d, cudaStream_t s) {
   const Ctx c = ctx_of<T>(k);
   DV<T> v = dv<T>(k);
   launch_matvec<T>(k, p, v.u, s, nullptr);
@@ -582,13 +584,31 @@ bem_status final_stats(bem_kernel_s* k, const T* p, double d, double* out5, cuda
   k_final_stats<T><<<c.rb, NTHREADS, 0, s>>>(p, v.u, v.f, k->ws.partials, k->ws.ticket, d, dout, c.n);
   note_launches(1);
   BEM_CUDA_TRY(cudaGetLastError());
-  BEM_CUDA_TRY(cudaMemcpyAsync(out5, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  BEM_CUDA_TRY(cudaMemcpyAsync(k->ws.aux_host, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
   return BEM_OK;
 }
 
+// Fills the scalar outputs from aux_host (after the stream has been synchronised).
+void fill_result(const bem_kernel_s* k, const bem_problem* prob, double d, bem_status st, bem_result* res) {
+  const double* fs = k->ws.aux_host;
+  const double delta2 = k->desc.delta * k->desc.delta;
+  res->matvecs += 1;
+  const double n_c = fs[3];
+  double gbar = 0.0;
+  if (prob->dgamma == 0.0 && prob->control == BEM_CTRL_FORCE && n_c > 0) gbar = fs[0] / n_c;
+  const double G = fmax(fs[1] - n_c * gbar * gbar, 0.0);
+  res->err_est = (fs[2] > 0.0) ? sqrt(G / fs[2]) : 0.0;
+  res->force = delta2 * fs[4];
+  res->depth = d;
+  res->n_contact = (int)n_c;
+  res->area = delta2 * n_c;
+  res->a_eq = sqrt(res->area / M_PI);
+  res->status = st;
+}
+
+// Initial state and first iterate of the Polonsky-Keer solve (asynchronous on s).
 template <typename T>
-bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cudaStream_t s) {
+bem_status pk_setup(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cudaStream_t s) {
   const Ctx c = ctx_of<T>(k);
   DV<T> v = dv<T>(k);
   SolveState* st = k->ws.state;
@@ -611,6 +631,9 @@ bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cuda
   init.n_neg = 1;  // no convergence test passes before one full iteration
   init.status = BEM_OK;
   init.mv_t_on = 1;
+  // products outside the iteration: one for the depth-control initial guess, or the
+  // first refresh of a warm or uniform start (counted here, run by the first iteration)
+  init.matvecs = 1;
   BEM_CUDA_TRY(cudaMemsetAsync(v.t, 0, c.n * sizeof(T), s));
   if (pinit != nullptr || force) {
     init.refresh = 1;
@@ -635,29 +658,77 @@ bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cuda
     note_launches(1);
   }
   BEM_CUDA_TRY(cudaGetLastError());
-  int extra_mv = (pinit == nullptr && !force) ? 1 : 0;
+  return BEM_OK;
+}
 
-  for (;;) {
-    for (int it = 0; it < CHUNK; ++it) {
-      launch_matvec<T>(k, v.p, v.u, s, &st->mv_p_on);
-      k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, st, c.n);
-      note_launches(1);
-      k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, part, tk, st, c.n);
-      note_launches(1);
-      k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
-      note_launches(1);
-      launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
-      k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
-      note_launches(1);
-      k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
-      note_launches(1);
-    }
-    BEM_CUDA_TRY(cudaGetLastError());
-    bem_status e = read_state<T>(k, s);
-    if (e != BEM_OK) return e;
-    if (hs->done) break;
+// CHUNK iterations of the Polonsky-Keer CG as plain launches.  Every launch is
+// gated by the device state, so iterations past convergence cost only their
+// launch; pointers and problem scalars live in the handle's device memory, which
+// makes the sequence independent of the problem and capturable once per handle.
+template <typename T>
+void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
+  const Ctx c = ctx_of<T>(k);
+  DV<T> v = dv<T>(k);
+  SolveState* st = k->ws.state;
+  double* part = k->ws.partials;
+  unsigned int* tk = k->ws.ticket;
+  for (int it = 0; it < CHUNK; ++it) {
+    launch_matvec<T>(k, v.p, v.u, s, &st->mv_p_on);
+    k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, st, c.n);
+    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, part, tk, st, c.n);
+    k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
+    launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
+    k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
+    k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
+    note_launches(5);
   }
-  hs->matvecs += extra_mv + ((pinit != nullptr || force) ? 1 : 0);
+}
+
+// One chunk: replay of the handle's captured graph when the stream allows capture
+// and pass timing is off (timing needs events around individual passes); plain
+// launches otherwise.  The first chunk on a handle always runs plainly, so one-time
+// kernel attributes are set outside any capture.
+template <typename T>
+bem_status pk_chunk(bem_kernel_s* k, cudaStream_t s) {
+  const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  if (!capturable || k->timing.on || !k->graphs.warm) {
+    pk_chunk_launches<T>(k, s);
+    k->graphs.warm = 1;
+    BEM_CUDA_TRY(cudaGetLastError());
+    return BEM_OK;
+  }
+  if (k->graphs.pk_exec == nullptr) {
+    cudaGraph_t g = nullptr;
+    const long long before = launches();
+    BEM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    pk_chunk_launches<T>(k, s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    k->graphs.pk_nodes = launches() - before;
+    note_launches(-k->graphs.pk_nodes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&k->graphs.pk_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      k->graphs.pk_exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  BEM_CUDA_TRY(cudaGraphLaunch(k->graphs.pk_exec, s));
+  note_launches(k->graphs.pk_nodes);
+  return BEM_OK;
+}
+
+template <typename T>
+bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cudaStream_t s) {
+  bem_status e = pk_setup<T>(k, prob, pinit, s);
+  if (e != BEM_OK) return e;
+  for (;;) {
+    e = pk_chunk<T>(k, s);
+    if (e != BEM_OK) return e;
+    e = read_state<T>(k, s);
+    if (e != BEM_OK) return e;
+    if (k->ws.state_host->done) break;
+  }
   return BEM_OK;
 }
 
@@ -768,24 +839,31 @@ __global__ void k_nonfinite(const T* __restrict__ a, const T* __restrict__ b, do
   if (grid_reduce<1>(v, partials, ticket, tot)) out[0] = tot[0];
 }
 
+// Counts non-finite entries of the height map (and warm start) into aux_host[7].
+template <typename T>
+bem_status nonfinite_launch(bem_kernel_s* k, const T* pinit, cudaStream_t s) {
+  const Ctx c = ctx_of<T>(k);
+  DV<T> v = dv<T>(k);
+  double* dout = k->ws.partials + 12 * RED_MAX_BLOCKS + 7;
+  k_nonfinite<T><<<c.rb, NTHREADS, 0, s>>>(v.f, pinit, k->ws.partials, k->ws.ticket, dout, c.n);
+  note_launches(1);
+  BEM_CUDA_TRY(cudaGetLastError());
+  BEM_CUDA_TRY(cudaMemcpyAsync(k->ws.aux_host + 7, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return BEM_OK;
+}
+
 template <typename T>
 bem_status solve_typed(bem_kernel_s* k, const bem_problem* prob, const T* f, const T* pinit, uint8_t* mask,
                        T* p_out, bem_result* res, cudaStream_t s) {
   DV<T> v = dv<T>(k);
   const size_t n = (size_t)k->N * k->N;
-  const double delta2 = k->desc.delta * k->desc.delta;
   if (f != v.f) BEM_CUDA_TRY(cudaMemcpyAsync(v.f, f, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   *res = bem_result{};
   {
-    const Ctx c = ctx_of<T>(k);
-    double* dout = k->ws.partials + 12 * RED_MAX_BLOCKS;
-    double bad = 0.0;
-    k_nonfinite<T><<<c.rb, NTHREADS, 0, s>>>(v.f, pinit, k->ws.partials, k->ws.ticket, dout, n);
-    note_launches(1);
-    BEM_CUDA_TRY(cudaGetLastError());
-    BEM_CUDA_TRY(cudaMemcpyAsync(&bad, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
+    bem_status e0 = nonfinite_launch<T>(k, pinit, s);
+    if (e0 != BEM_OK) return e0;
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (bad > 0.0) {
+    if (k->ws.aux_host[7] > 0.0) {
       set_error("non-finite value in the height map or the warm start");
       res->status = BEM_ENAN;
       return BEM_ENAN;
@@ -814,21 +892,10 @@ bem_status solve_typed(bem_kernel_s* k, const bem_problem* prob, const T* f, con
     if (st == BEM_OK) st = (bem_status)hs->status;
     psol = v.p;
   }
-  double fs[5];
-  bem_status e = final_stats<T>(k, psol, d, fs, s);
+  bem_status e = final_stats_launch<T>(k, psol, d, s);
   if (e != BEM_OK) return e;
-  res->matvecs += 1;
-  const double n_c = fs[3];
-  double gbar = 0.0;
-  if (prob->dgamma == 0.0 && prob->control == BEM_CTRL_FORCE && n_c > 0) gbar = fs[0] / n_c;
-  const double G = fmax(fs[1] - n_c * gbar * gbar, 0.0);
-  res->err_est = (fs[2] > 0.0) ? sqrt(G / fs[2]) : 0.0;
-  res->force = delta2 * fs[4];
-  res->depth = d;
-  res->n_contact = (int)n_c;
-  res->area = delta2 * n_c;
-  res->a_eq = sqrt(res->area / M_PI);
-  res->status = st;
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  fill_result(k, prob, d, st, res);
   if (p_out != nullptr && p_out != psol)
     BEM_CUDA_TRY(cudaMemcpyAsync(p_out, psol, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   if (st == BEM_ENOCONV) set_error("iteration limit reached before the tolerance");
@@ -836,7 +903,74 @@ bem_status solve_typed(bem_kernel_s* k, const bem_problem* prob, const T* f, con
   return st;
 }
 
+// Non-adhesive instances solved concurrently: instance i works on strm[i]; each
+// round launches one chunk (a graph replay) per unfinished instance and then
+// reads every instance's state; the height maps and warm starts are already in
+// the handles' f and x slots.
+template <typename T>
+bem_status batch_typed(int n, bem_kernel_s* const* ks, const bem_problem* probs, const bool* has_pinit,
+                       bem_result* res, cudaStream_t const* strm) {
+  std::vector<int> active;
+  for (int i = 0; i < n; ++i) {
+    res[i] = bem_result{};
+    bem_status e = nonfinite_launch<T>(ks[i], has_pinit[i] ? dv<T>(ks[i]).x : nullptr, strm[i]);
+    if (e != BEM_OK) return e;
+  }
+  for (int i = 0; i < n; ++i) BEM_CUDA_TRY(cudaStreamSynchronize(strm[i]));
+  for (int i = 0; i < n; ++i) {
+    if (ks[i]->ws.aux_host[7] > 0.0) {
+      res[i].status = BEM_ENAN;
+      continue;
+    }
+    bem_status e = pk_setup<T>(ks[i], &probs[i], has_pinit[i] ? dv<T>(ks[i]).x : nullptr, strm[i]);
+    if (e != BEM_OK) return e;
+    active.push_back(i);
+  }
+  std::vector<int> next, finished;
+  while (!active.empty()) {
+    for (int i : active) {
+      bem_kernel_s* k = ks[i];
+      bem_status e = pk_chunk<T>(k, strm[i]);
+      if (e != BEM_OK) return e;
+      BEM_CUDA_TRY(cudaMemcpyAsync(k->ws.state_host, k->ws.state, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                                   strm[i]));
+      BEM_CUDA_TRY(cudaEventRecord(k->ws.done_ev, strm[i]));
+    }
+    next.clear();
+    for (int i : active) {
+      BEM_CUDA_TRY(cudaEventSynchronize(ks[i]->ws.done_ev));
+      if (ks[i]->timing.on) harvest_pass_timing(ks[i]);
+      if (ks[i]->ws.state_host->done) finished.push_back(i);
+      else next.push_back(i);
+    }
+    active.swap(next);
+  }
+  for (int i : finished) {
+    const SolveState* hs = ks[i]->ws.state_host;
+    res[i].iters = hs->iter;
+    res[i].outer_iters = 1;
+    res[i].matvecs = hs->matvecs;
+    res[i].residual = hs->res;
+    res[i].status = hs->status;
+    bem_status e = final_stats_launch<T>(ks[i], dv<T>(ks[i]).p, hs->d, strm[i]);
+    if (e != BEM_OK) return e;
+  }
+  for (int i : finished) BEM_CUDA_TRY(cudaStreamSynchronize(strm[i]));
+  for (int i : finished) {
+    const SolveState* hs = ks[i]->ws.state_host;
+    fill_result(ks[i], &probs[i], hs->d, (bem_status)hs->status, &res[i]);
+  }
+  return BEM_OK;
+}
+
 }  // namespace
+
+bem_status solve_batch_device(int n, bem_kernel_s* const* ks, const bem_problem* probs, const bool* has_pinit,
+                              bem_result* res, cudaStream_t const* strm) {
+  if (n == 0) return BEM_OK;
+  if (ks[0]->prec == BEM_FP64) return batch_typed<double>(n, ks, probs, has_pinit, res, strm);
+  return batch_typed<float>(n, ks, probs, has_pinit, res, strm);
+}
 
 bem_status solve_contact_device(bem_kernel_s* k, const bem_problem* prob, const void* f, const void* pinit,
                                 uint8_t* mask, void* p_out, bem_result* res, cudaStream_t s) {

@@ -179,3 +179,64 @@ def test_batch_matches_single_solves(cuda):
         assert rb["force"] == r["force"] and rb["iters"] == r["iters"]
     for k in ks:
         k.close()
+
+
+def test_batch_heterogeneous_concurrent(cuda):
+    """Rough-surface batch workload at small sizes: 12 instances of N in {64, 128, 256},
+    solved concurrently by bem_solve_batch; each equals its single solve bit for bit,
+    and one instance is compared with the oracle."""
+    insts = [inputs.batch_instance(20260100 + i, sizes=(64, 128, 256)) for i in range(12)]
+    ks, probs, outs, hts, singles = [], [], [], [], []
+    for inst in insts:
+        k = bem.Kernel(inst["N"], inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"],
+                       precision="fp32")
+        ht = torch.tensor(inst["height"], device=cuda, dtype=torch.float32)
+        p, r = k.solve(ht, "force", inst["force"], tol=1e-8)
+        singles.append((p.clone(), r))
+        ks.append(k)
+        hts.append(ht)
+        outs.append(torch.empty_like(ht))
+        probs.append(bem.make_problem(ht, bem.BEM_CTRL_FORCE, inst["force"], tol=1e-8))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        st, res = bem.bem_solve_batch([k.handle for k in ks], probs, outs, stream=s)
+    s.synchronize()
+    assert st == 0
+    for (p, r), o, rb in zip(singles, outs, res):
+        assert rb["status"] == 0
+        assert torch.equal(p, o)
+        assert rb["iters"] == r["iters"] and rb["matvecs"] == r["matvecs"]
+    inst = insts[0]
+    mv = oracle_mv(inst["N"], inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"])
+    ref = contact.solve_nonadhesive(mv, inst["height"], inst["delta"], "force", inst["force"], tol=1e-13)
+    assert rel(outs[0].double().cpu().numpy(), ref["p"]) < 2e-4
+    for k in ks:
+        k.close()
+
+
+def test_batch_rejects_duplicate_handles(cuda):
+    c, f = sphere_case(16)
+    with bem.Kernel(16, c["delta"], c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"]) as k:
+        ft = torch.tensor(f, device=cuda)
+        prob = bem.make_problem(ft, bem.BEM_CTRL_DEPTH, c["d"])
+        st, _ = bem.bem_solve_batch([k.handle, k.handle], [prob, prob], [torch.empty_like(ft), torch.empty_like(ft)])
+        assert st == bem.BEM_EINVAL
+
+
+def test_graph_replay_equals_plain_launches(cuda):
+    """A solve on a non-default stream replays the handle's captured iteration graph;
+    the result equals the plain-launch solve on the default stream."""
+    inst = inputs.batch_instance(20260200, sizes=(128,))
+    with bem.Kernel(128, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"],
+                    precision="fp32") as k:
+        ht = torch.tensor(inst["height"], device=cuda, dtype=torch.float32)
+        p0, r0 = k.solve(ht, "force", inst["force"], tol=1e-8)
+        s = torch.cuda.Stream()
+        outs = []
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                p1, r1 = k.solve(ht, "force", inst["force"], tol=1e-8, stream=s)
+                outs.append((p1.clone(), r1))
+        s.synchronize()
+    for p1, r1 in outs:
+        assert torch.equal(p0, p1) and r0["iters"] == r1["iters"]
