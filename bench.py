@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=48, help="instances of the batch workload (0: skip)")
     return ap.parse_args()
 
 
@@ -158,6 +159,50 @@ def make_instances(torch, dev, bem, inputs):
         f = torch.tensor(inst["height"], dtype=torch.float32, device=dev)
         out.append(dict(inst=inst, kernel=k, f=f, p=torch.empty_like(f)))
     return out
+
+
+BATCH_SEED0 = 20260000
+
+
+def batch_bench(torch, dev, bem, inputs, n_inst):
+    """Rough-surface batch workload: n_inst instances, N drawn from {128, 256, 512, 1024},
+    FP32, force control to 1e-8; one bem_solve_batch call against the same instances
+    solved one after another on one stream (both replay the handles' iteration graphs)."""
+    insts = [inputs.batch_instance(BATCH_SEED0 + i) for i in range(n_inst)]
+    ks, probs, hts, outs = [], [], [], []
+    for inst in insts:
+        k = bem.Kernel(inst["N"], inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"],
+                       precision="fp32")
+        ht = torch.tensor(inst["height"], dtype=torch.float32, device=dev)
+        ks.append(k)
+        hts.append(ht)
+        outs.append(torch.empty_like(ht))
+        probs.append(bem.make_problem(ht, bem.BEM_CTRL_FORCE, inst["force"], tol=TOL, max_iter=5000))
+    s = torch.cuda.Stream(device=dev)
+    handles = [k.handle for k in ks]
+    with torch.cuda.stream(s):
+        st, _ = bem.bem_solve_batch(handles, probs, outs, stream=s)          # warm-up: graphs captured
+        s.synchronize()
+        t0 = time.perf_counter()
+        st, res = bem.bem_solve_batch(handles, probs, outs, stream=s)
+        s.synchronize()
+        t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        seq = [bem.bem_solve_contact(k.handle, pr, o, stream=s) for k, pr, o in zip(ks, probs, outs)]
+        s.synchronize()
+        t_seq = time.perf_counter() - t0
+    mv = sum(r["matvecs"] for r in res)
+    sizes = {}
+    for inst in insts:
+        sizes[inst["N"]] = sizes.get(inst["N"], 0) + 1
+    for k in ks:
+        k.close()
+    return {"instances": n_inst, "sizes": {str(a): b for a, b in sorted(sizes.items())}, "status": int(st),
+            "all_converged": all(r["status"] == 0 for r in res),
+            "batch_wall_ms": 1000 * t_batch, "sequential_wall_ms": 1000 * t_seq,
+            "speedup": t_seq / t_batch, "instances_per_s": n_inst / t_batch,
+            "matvecs": mv, "matvecs_per_s": mv / t_batch,
+            "seeds": f"{BATCH_SEED0}..{BATCH_SEED0 + n_inst - 1}"}
 
 
 def cpu_oracle_matvecs(seconds_hint=True):
@@ -328,6 +373,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if args.batch > 0:
+        line["batch"] = batch_bench(torch, dev, bem, inputs, args.batch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt = cpu_oracle_matvecs()
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
