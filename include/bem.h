@@ -175,6 +175,52 @@ bem_status bem_matvec_static(const bem_kernel_desc* desc, const float* p, float*
 bem_status bem_set_pass_timing(bem_kernel k, int32_t on);
 bem_status bem_pass_timing(bem_kernel k, double* ms_total, int64_t* launches, int32_t reset);
 
+/* ---- Learned warm start (no counterpart in the paper) --------------------------
+ * A Fourier neural operator that predicts a dimensionless pressure field q = p/pbar
+ * (pbar = F / L^2) from 7 per-cell features, used as the starting pressure of the
+ * contact solve.  Layers: pointwise lift 7 -> width; `layers` blocks
+ * z = S(v) + W v + b, v' = gelu(z) (no gelu after the last); projection
+ * h = gelu(Q1 v + q1) (width -> hidden), out = Q2 h + q2 (hidden -> 1).  S keeps the
+ * Fourier modes kx in {0..m-1, N-m..N-1}, ky in {0..m-1} (m = modes) of each channel,
+ * mixes channels with a complex width x width matrix per mode and transforms back
+ * (half-spectrum weights 1 for ky = 0, 2 otherwise, factor 1/N^2).  Weights are
+ * float masters with a bfloat16 copy used by every kernel; all accumulation is
+ * float.  Arrays are device arrays, channels-first: features [B][7][N][N],
+ * outputs [B][N][N].  Parameter vector order: P [width][7], p [width],
+ * R_re [layers][width][width][2m][m], R_im (same), W [layers][width][width],
+ * b [layers][width], Q1 [hidden][width], q1 [hidden], Q2 [hidden], q2 [1].
+ * width and hidden must be one of 1, 7, 8, 16, 32, 64; N >= 2 modes. */
+typedef struct {
+  int32_t width, modes, layers, hidden;
+} bem_fno_desc;
+typedef struct bem_fno_s* bem_fno;
+bem_status bem_fno_create(const bem_fno_desc* desc, bem_fno* out);
+bem_status bem_fno_destroy(bem_fno f);
+int64_t bem_fno_param_count(bem_fno f);
+/* copy in float parameters (host or device); resets the optimiser state */
+bem_status bem_fno_set_params(bem_fno f, const float* params, int64_t count, void* cuda_stream);
+/* copy out the float masters (rounded = 0) or the bfloat16 values in use (rounded = 1) */
+bem_status bem_fno_get_params(bem_fno f, float* params, int64_t count, int32_t rounded, void* cuda_stream);
+/* features of B samples: heights [B][N][N]; params [B][4] doubles (h/delta, E1/E2, nu1,
+ * nu2) -> x [B][7][N][N]: height standardised per sample, log(h/delta)/log 200,
+ * log(E1/E2)/log 20, nu1, nu2, (column + 1/2)/N, (row + 1/2)/N.  B <= 4096. */
+bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* heights, const double* params, float* x,
+                            void* cuda_stream);
+bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, float* out, void* cuda_stream);
+/* forward + backward of the loss mean((out - target)^2); writes the gradient (host or
+ * device, may be NULL) and the loss; synchronises the stream */
+bem_status bem_fno_gradients(bem_fno f, int32_t B, int32_t N, const float* x, const float* target, float* grad,
+                             double* loss, void* cuda_stream);
+/* one Adam step (beta 0.9/0.999, eps 1e-8) on the loss above */
+bem_status bem_fno_train_step(bem_fno f, int32_t B, int32_t N, const float* x, const float* target, float lr,
+                              double* loss, void* cuda_stream);
+/* training target q = p / pbar[b] (pbar: B doubles, device) */
+bem_status bem_fno_target(bem_fno f, int32_t B, int32_t N, const float* p, const double* pbar, float* q,
+                          void* cuda_stream);
+/* warm-start pressure p = pbar[b] * max(out, 0) (pbar: B doubles, device) */
+bem_status bem_fno_pressure(bem_fno f, int32_t B, int32_t N, const float* out, const double* pbar, float* p,
+                            void* cuda_stream);
+
 /* Number of kernel launches the library has issued since it was loaded. */
 int64_t bem_launch_count(void);
 

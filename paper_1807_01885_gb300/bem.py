@@ -27,7 +27,9 @@ BEM_DC_FINITE_PART, BEM_DC_ZERO = 0, 1
 # entry points declared in include/bem.h
 EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
            "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_set_pass_timing", "bem_pass_timing",
-           "bem_launch_count", "bem_last_error", "bem_version")
+           "bem_launch_count", "bem_last_error", "bem_version", "bem_fno_create", "bem_fno_destroy",
+           "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features", "bem_fno_forward",
+           "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure")
 BEM_STATIC_MAX_N = 256
 
 
@@ -41,6 +43,11 @@ class KernelDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("precision", ctypes.c_int32), ("dc_mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("delta", ctypes.c_double), ("h", ctypes.c_double),
                 ("E1", ctypes.c_double), ("nu1", ctypes.c_double), ("E2", ctypes.c_double), ("nu2", ctypes.c_double)]
+
+
+class FnoDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("modes", ctypes.c_int32), ("layers", ctypes.c_int32),
+                ("hidden", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -91,6 +98,22 @@ def load(path=None):
     lib.bem_profile_passes.restype = i32
     lib.bem_launch_count.argtypes = []
     lib.bem_matvec_static.argtypes = [ctypes.POINTER(KernelDesc), vp, vp, vp]
+    i64, dbl = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    lib.bem_fno_create.argtypes = [ctypes.POINTER(FnoDesc), ctypes.POINTER(vp)]
+    lib.bem_fno_destroy.argtypes = [vp]
+    lib.bem_fno_param_count.argtypes = [vp]
+    lib.bem_fno_param_count.restype = i64
+    lib.bem_fno_set_params.argtypes = [vp, vp, i64, vp]
+    lib.bem_fno_get_params.argtypes = [vp, vp, i64, i32, vp]
+    lib.bem_fno_features.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    lib.bem_fno_forward.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.bem_fno_gradients.argtypes = [vp, i32, i32, vp, vp, vp, dbl, vp]
+    lib.bem_fno_train_step.argtypes = [vp, i32, i32, vp, vp, ctypes.c_float, dbl, vp]
+    lib.bem_fno_target.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    lib.bem_fno_pressure.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    for name in ("bem_fno_create", "bem_fno_destroy", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features",
+                 "bem_fno_forward", "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure"):
+        getattr(lib, name).restype = i32
     lib.bem_set_pass_timing.argtypes = [vp, i32]
     lib.bem_set_pass_timing.restype = i32
     lib.bem_pass_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
@@ -276,3 +299,59 @@ class Kernel:
     def __exit__(self, *a):
         self.close()
 
+
+class Fno:
+    """Owning wrapper of a bem_fno handle (the warm-start network)."""
+
+    def __init__(self, width=32, modes=16, layers=4, hidden=64):
+        self.desc = FnoDesc(width=width, modes=modes, layers=layers, hidden=hidden)
+        out = ctypes.c_void_p()
+        _check(load().bem_fno_create(ctypes.byref(self.desc), ctypes.byref(out)))
+        self.handle = out.value
+        self.count = load().bem_fno_param_count(self.handle)
+
+    def set_params(self, w, stream=None):
+        _check(load().bem_fno_set_params(self.handle, _ptr(w), self.count, _stream(stream)))
+
+    def get_params(self, out, rounded=False, stream=None):
+        _check(load().bem_fno_get_params(self.handle, _ptr(out), self.count, 1 if rounded else 0, _stream(stream)))
+        return out
+
+    def features(self, B, N, heights, params, x, stream=None):
+        _check(load().bem_fno_features(self.handle, B, N, _ptr(heights), _ptr(params), _ptr(x), _stream(stream)))
+        return x
+
+    def forward(self, B, N, x, out, stream=None):
+        _check(load().bem_fno_forward(self.handle, B, N, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def gradients(self, B, N, x, target, grad=None, stream=None):
+        loss = ctypes.c_double()
+        _check(load().bem_fno_gradients(self.handle, B, N, _ptr(x), _ptr(target), _ptr(grad), ctypes.byref(loss),
+                                        _stream(stream)))
+        return loss.value
+
+    def train_step(self, B, N, x, target, lr, stream=None):
+        loss = ctypes.c_double()
+        _check(load().bem_fno_train_step(self.handle, B, N, _ptr(x), _ptr(target), ctypes.c_float(lr),
+                                         ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def target(self, B, N, p, pbar, q, stream=None):
+        _check(load().bem_fno_target(self.handle, B, N, _ptr(p), _ptr(pbar), _ptr(q), _stream(stream)))
+        return q
+
+    def pressure(self, B, N, out, pbar, p, stream=None):
+        _check(load().bem_fno_pressure(self.handle, B, N, _ptr(out), _ptr(pbar), _ptr(p), _stream(stream)))
+        return p
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().bem_fno_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,806 @@
+// Fourier-neural-operator warm start: forward, backward and Adam on the GPU.
+//
+// The network (layers defined in include/bem.h, bem_fno_*): a pointwise lift from 7
+// input features to W channels, L layers z = S(v) + W_l v + b_l with v' = gelu(z)
+// (no gelu after the last), and a projection h = gelu(Q1 v + q1), out = Q2 h + q2.
+// S is the spectral convolution on the retained modes kx in {0..m-1, N-m..N-1},
+// ky in {0..m-1}: a truncated DFT of each channel, a complex W x W mixing per mode
+// and the truncated inverse with half-spectrum weights c_0 = 1, c_ky = 2.
+//
+// Precision: parameters are kept in float (master copy, Adam state) and used by every
+// kernel from a bfloat16 copy refreshed after each update; activations, gradients and
+// all accumulations are float (bf16 in, fp32 accumulate).  The truncated transforms
+// are direct sums against a float twiddle table (the retained modes are few, so the
+// O(N m) sums are cheaper than full FFTs).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+namespace {
+
+constexpr int FT = 256;   // threads per block
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ float b2f(bf16 x) { return __bfloat162float(x); }
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+int blocks_for(size_t n) { return (int)std::min<size_t>((n + FT - 1) / FT, 65535u * 16u); }
+
+#define FOR_N(i, n) for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------
+// inputs
+
+// per-sample mean and standard deviation of the height map (one block per sample)
+__global__ void k_fno_moments(const float* __restrict__ f, float* __restrict__ mom, size_t P) {
+  const float* fb = f + blockIdx.x * P;
+  double s = 0.0, s2 = 0.0;   // a few values per thread, once per call
+  for (size_t i = threadIdx.x; i < P; i += blockDim.x) {
+    const double v = fb[i];
+    s += v;
+    s2 += v * v;
+  }
+  __shared__ double sh[2][FT];
+  sh[0][threadIdx.x] = s;
+  sh[1][threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = FT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = sh[0][0] / (double)P;
+    const double var = fmax(sh[1][0] / (double)P - mean * mean, 1e-30);
+    mom[2 * blockIdx.x] = (float)mean;
+    mom[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var));
+  }
+}
+
+// x[b][0] = normalised height, [1] = log(h/delta)/log 200, [2] = log(E1/E2)/log 20,
+// [3] = nu1, [4] = nu2, [5] = (c + 1/2)/N, [6] = (r + 1/2)/N
+__global__ void k_fno_features(const float* __restrict__ f, const float* __restrict__ mom,
+                               const double* __restrict__ sp, float* __restrict__ x, int N, int B) {
+  const size_t P = (size_t)N * N;
+  FOR_N(i, (size_t)B * P) {
+    const int b = (int)(i / P);
+    const size_t pix = i % P;
+    const int r = (int)(pix / N), c = (int)(pix % N);
+    float* xb = x + (size_t)b * 7 * P;
+    xb[pix] = (f[i] - mom[2 * b]) * mom[2 * b + 1];
+    xb[P + pix] = (float)(log(sp[4 * b]) / log(200.0));
+    xb[2 * P + pix] = (float)(log(sp[4 * b + 1]) / log(20.0));
+    xb[3 * P + pix] = (float)sp[4 * b + 2];
+    xb[4 * P + pix] = (float)sp[4 * b + 3];
+    xb[5 * P + pix] = ((float)c + 0.5f) / (float)N;
+    xb[6 * P + pix] = ((float)r + 0.5f) / (float)N;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pointwise (1x1) layers: Y[b][o][p] = bias[o] + sum_c W[o][c] X[b][c][p]
+// TRANS: use W^T (backward data pass: W stored [Cout_fwd][Cin_fwd], here o = c_fwd).
+template <int CIN, bool TRANS, bool ACCUM, bool GELU>
+__global__ void k_pw(const float* __restrict__ X, const bf16* __restrict__ Wt, const bf16* __restrict__ bias,
+                     float* __restrict__ Y, float* __restrict__ Yact, int cout, size_t P) {
+  extern __shared__ float wsh[];
+  for (int i = threadIdx.x; i < cout * CIN; i += blockDim.x) {
+    const int o = i / CIN, c = i % CIN;
+    wsh[i] = TRANS ? b2f(Wt[(size_t)c * cout + o]) : b2f(Wt[i]);
+  }
+  __syncthreads();
+  const int b = blockIdx.y;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float xr[CIN];
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) xr[c] = X[((size_t)b * CIN + c) * P + p];
+  for (int o = 0; o < cout; ++o) {
+    float acc = bias != nullptr ? b2f(bias[o]) : 0.f;
+    const float* w = wsh + o * CIN;
+#pragma unroll
+    for (int c = 0; c < CIN; ++c) acc = fmaf(w[c], xr[c], acc);
+    float* y = Y + ((size_t)b * cout + o) * P + p;
+    if (ACCUM) acc += *y;
+    *y = acc;
+    if (GELU) Yact[((size_t)b * cout + o) * P + p] = gelu_f(acc);
+  }
+}
+
+// weight gradient partials: per block of FT pixels (of one sample) the Cout x Cin
+// products and the Cout bias sums; summed over blocks by k_pw_wgrad_sum
+__global__ void k_pw_wgrad(const float* __restrict__ dY, const float* __restrict__ X, float* __restrict__ part,
+                           int cout, int cin, size_t P) {
+  extern __shared__ float sh[];
+  float* dys = sh;                 // [cout][FT]
+  float* xs = sh + cout * FT;      // [cin][FT]
+  const int b = blockIdx.y;
+  const size_t p0 = blockIdx.x * (size_t)FT;
+  const int np = (int)std::min<size_t>(FT, P - p0);
+  for (int o = 0; o < cout; ++o)
+    dys[o * FT + threadIdx.x] = (int)threadIdx.x < np ? dY[((size_t)b * cout + o) * P + p0 + threadIdx.x] : 0.f;
+  for (int c = 0; c < cin; ++c)
+    xs[c * FT + threadIdx.x] = (int)threadIdx.x < np ? X[((size_t)b * cin + c) * P + p0 + threadIdx.x] : 0.f;
+  __syncthreads();
+  const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  const int nout = cout * cin + cout;
+  for (int e = threadIdx.x; e < nout; e += blockDim.x) {
+    float acc = 0.f;
+    if (e < cout * cin) {
+      const int o = e / cin, c = e % cin;
+      for (int k = 0; k < FT; ++k) acc = fmaf(dys[o * FT + k], xs[c * FT + k], acc);
+    } else {
+      const int o = e - cout * cin;
+      for (int k = 0; k < FT; ++k) acc += dys[o * FT + k];
+    }
+    part[blk * nout + e] = acc;
+  }
+}
+
+__global__ void k_pw_wgrad_sum(const float* __restrict__ part, int nblk, int cout, int cin, float* __restrict__ gw,
+                               float* __restrict__ gb) {
+  const int nout = cout * cin + cout;
+  FOR_N(e, (size_t)nout) {
+    float acc = 0.f;
+    for (int k = 0; k < nblk; ++k) acc += part[(size_t)k * nout + e];
+    if (e < (size_t)cout * cin) gw[e] = acc;
+    else gb[e - (size_t)cout * cin] = acc;
+  }
+}
+
+__global__ void k_gelu_bwd(const float* __restrict__ dv, const float* __restrict__ z, float* __restrict__ dz, size_t n) {
+  FOR_N(i, n) dz[i] = dv[i] * gelu_grad_f(z[i]);
+}
+
+__global__ void k_gelu_fwd(const float* __restrict__ z, float* __restrict__ v, size_t n) {
+  FOR_N(i, n) v[i] = gelu_f(z[i]);
+}
+
+// ---------------------------------------------------------------------------
+// truncated transforms; tw[k] = e^{-2 pi i k / N}
+
+__device__ __forceinline__ int kx_of(int kxi, int m, int N) { return kxi < m ? kxi : N - 2 * m + kxi; }
+
+// A[row][ky] = sum_y v[row][y] e^{-2 pi i ky y/N},  ky < m
+__global__ void k_dft_y(const float* __restrict__ v, float2* __restrict__ A, const float2* __restrict__ tw, int N,
+                        int m, size_t rows) {
+  FOR_N(i, rows * m) {
+    const size_t row = i / m;
+    const int ky = (int)(i % m);
+    const float* vr = v + row * N;
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int y = 0; y < N; ++y) {
+      const float2 w = tw[idx];
+      re = fmaf(vr[y], w.x, re);
+      im = fmaf(vr[y], w.y, im);
+      idx += ky;
+      if (idx >= N) idx -= N;
+    }
+    A[i] = make_float2(re, im);
+  }
+}
+
+// Xh[bc][kxi][ky] = wky[ky] * sum_x A[bc][x][ky] e^{-2 pi i kx x/N}   (wky may be null)
+__global__ void k_dft_x(const float2* __restrict__ A, float2* __restrict__ Xh, const float2* __restrict__ tw,
+                        const float* __restrict__ wky, int N, int m, size_t bc) {
+  const int nm = 2 * m * m;
+  FOR_N(i, bc * nm) {
+    const size_t q = i / nm;
+    const int mode = (int)(i % nm);
+    const int kxi = mode / m, ky = mode % m;
+    const int kx = kx_of(kxi, m, N);
+    const float2* a = A + q * (size_t)N * m + ky;
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int x = 0; x < N; ++x) {
+      const float2 w = tw[idx];
+      const float2 v = a[(size_t)x * m];
+      re += v.x * w.x - v.y * w.y;
+      im += v.x * w.y + v.y * w.x;
+      idx += kx;
+      if (idx >= N) idx -= N;
+    }
+    const float s = wky != nullptr ? wky[ky] : 1.f;
+    Xh[i] = make_float2(re * s, im * s);
+  }
+}
+
+// A[bc][x][ky] = sum_kxi Y[bc][kxi][ky] e^{+2 pi i kx x/N}
+__global__ void k_idft_x(const float2* __restrict__ Y, float2* __restrict__ A, const float2* __restrict__ tw, int N,
+                         int m, size_t bc) {
+  FOR_N(i, bc * (size_t)N * m) {
+    const size_t q = i / ((size_t)N * m);
+    const int rem = (int)(i % ((size_t)N * m));
+    const int x = rem / m, ky = rem % m;
+    const float2* y = Y + q * 2 * m * m + ky;
+    float re = 0.f, im = 0.f;
+    for (int kxi = 0; kxi < 2 * m; ++kxi) {
+      const int kx = kx_of(kxi, m, N);
+      const float2 w = tw[(int)(((long long)kx * x) % N)];   // e^{-i theta}; conjugate below
+      const float2 v = y[(size_t)kxi * m];
+      re += v.x * w.x + v.y * w.y;
+      im += v.y * w.x - v.x * w.y;
+    }
+    A[i] = make_float2(re, im);
+  }
+}
+
+// out[row][y] (=|+=) scale * sum_ky c[ky] Re(A[row][ky] e^{+2 pi i ky y/N})   (c may be null: 1)
+template <bool ACCUM>
+__global__ void k_idft_y(const float2* __restrict__ A, float* __restrict__ out, const float2* __restrict__ tw,
+                         const float* __restrict__ c, float scale, int N, int m, size_t rows) {
+  FOR_N(i, rows * N) {
+    const size_t row = i / N;
+    const int y = (int)(i % N);
+    const float2* a = A + row * m;
+    float acc = 0.f;
+    int idx = 0;
+    for (int ky = 0; ky < m; ++ky) {
+      const float2 w = tw[idx];   // e^{-i ky y theta}
+      const float2 v = a[ky];
+      const float re = v.x * w.x + v.y * w.y;   // Re(v conj(w))
+      acc = fmaf(c != nullptr ? c[ky] : 1.f, re, acc);
+      idx += y;
+      if (idx >= N) idx -= N;
+    }
+    acc *= scale;
+    if (ACCUM) out[i] += acc;
+    else out[i] = acc;
+  }
+}
+
+// Y[b][o][mode] = sum_i X[b][i][mode] R[i][o][mode]
+__global__ void k_mix(const float2* __restrict__ X, const bf16* __restrict__ Rre, const bf16* __restrict__ Rim,
+                      float2* __restrict__ Y, int W, int nm, int B) {
+  FOR_N(e, (size_t)B * W * nm) {
+    const int mode = (int)(e % nm);
+    const int o = (int)((e / nm) % W);
+    const int b = (int)(e / ((size_t)nm * W));
+    float re = 0.f, im = 0.f;
+    for (int i = 0; i < W; ++i) {
+      const float2 x = X[((size_t)b * W + i) * nm + mode];
+      const size_t r = ((size_t)i * W + o) * nm + mode;
+      const float rr = b2f(Rre[r]), ri = b2f(Rim[r]);
+      re += x.x * rr - x.y * ri;
+      im += x.x * ri + x.y * rr;
+    }
+    Y[e] = make_float2(re, im);
+  }
+}
+
+// dR[i][o][mode] = sum_b conj(X[b][i][mode]) dY[b][o][mode]
+__global__ void k_mix_wgrad(const float2* __restrict__ X, const float2* __restrict__ dY, float* __restrict__ gre,
+                            float* __restrict__ gim, int W, int nm, int B) {
+  FOR_N(e, (size_t)W * W * nm) {
+    const int mode = (int)(e % nm);
+    const int o = (int)((e / nm) % W);
+    const int i = (int)(e / ((size_t)nm * W));
+    float re = 0.f, im = 0.f;
+    for (int b = 0; b < B; ++b) {
+      const float2 x = X[((size_t)b * W + i) * nm + mode];
+      const float2 d = dY[((size_t)b * W + o) * nm + mode];
+      re += x.x * d.x + x.y * d.y;
+      im += x.x * d.y - x.y * d.x;
+    }
+    gre[e] = re;
+    gim[e] = im;
+  }
+}
+
+// dX[b][i][mode] = sum_o conj(R[i][o][mode]) dY[b][o][mode]
+__global__ void k_mix_dgrad(const float2* __restrict__ dY, const bf16* __restrict__ Rre, const bf16* __restrict__ Rim,
+                            float2* __restrict__ dX, int W, int nm, int B) {
+  FOR_N(e, (size_t)B * W * nm) {
+    const int mode = (int)(e % nm);
+    const int i = (int)((e / nm) % W);
+    const int b = (int)(e / ((size_t)nm * W));
+    float re = 0.f, im = 0.f;
+    for (int o = 0; o < W; ++o) {
+      const float2 d = dY[((size_t)b * W + o) * nm + mode];
+      const size_t r = ((size_t)i * W + o) * nm + mode;
+      const float rr = b2f(Rre[r]), ri = b2f(Rim[r]);
+      re += rr * d.x + ri * d.y;
+      im += rr * d.y - ri * d.x;
+    }
+    dX[e] = make_float2(re, im);
+  }
+}
+
+// loss = mean (out - t)^2 (block partials), d_out = 2 (out - t) / n
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t, float* __restrict__ dout,
+                      double* __restrict__ part, size_t n) {
+  double s = 0.0;
+  FOR_N(i, n) {
+    const float d = out[i] - t[i];
+    dout[i] = 2.f * d / (float)n;
+    s += (double)d * d;
+  }
+  __shared__ double sh[FT];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = FT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, bf16* __restrict__ wb, size_t n, float lr, float b1, float b2,
+                       float c1, float c2, float eps) {
+  FOR_N(i, n) {
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float wn = w[i] - lr * (a * c1) / (sqrtf(v * c2) + eps);
+    w[i] = wn;
+    wb[i] = __float2bfloat16(wn);
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ w, bf16* __restrict__ wb, size_t n) {
+  FOR_N(i, n) wb[i] = __float2bfloat16(w[i]);
+}
+
+__global__ void k_bf16_to_f32(const bf16* __restrict__ wb, float* __restrict__ w, size_t n) {
+  FOR_N(i, n) w[i] = b2f(wb[i]);
+}
+
+// p_init[b][p] = pbar[b] * max(out[b][p], 0)
+__global__ void k_fno_pressure(const float* __restrict__ out, const double* __restrict__ pbar, float* __restrict__ p,
+                               size_t P, int B) {
+  FOR_N(i, (size_t)B * P) {
+    const float q = out[i];
+    p[i] = q > 0.f ? (float)pbar[i / P] * q : 0.f;
+  }
+}
+
+// q[b][p] = p[b][p] / pbar[b]  (training targets)
+__global__ void k_fno_target(const float* __restrict__ p, const double* __restrict__ pbar, float* __restrict__ q,
+                             size_t P, int B) {
+  FOR_N(i, (size_t)B * P) q[i] = (float)((double)p[i] / pbar[i / P]);
+}
+
+__global__ void k_twiddle_f(float2* __restrict__ tw, int N) {
+  FOR_N(k, (size_t)N) {
+    double s, c;
+    sincospi(2.0 * (double)k / (double)N, &s, &c);
+    tw[k] = make_float2((float)c, (float)(-s));
+  }
+}
+
+}  // namespace
+}  // namespace bem
+
+// ===========================================================================
+using namespace bem;
+
+struct bem_fno_s {
+  bem_fno_desc d;
+  int dev = 0;
+  size_t o_Pw, o_Pb, o_Rre, o_Rim, o_Ww, o_Wb, o_Q1w, o_Q1b, o_Q2w, o_Q2b, P;
+  float* w = nullptr;       // master weights
+  bf16* wb = nullptr;       // bf16 copy used by the kernels
+  float* g = nullptr;       // gradients
+  float* m1 = nullptr;
+  float* m2 = nullptr;
+  int step = 0;
+  // activations and scratch, sized for (B, N) of the largest call so far
+  int capB = 0, capN = 0, twN = 0;
+  bool cap_train = false;
+  std::vector<float*> v, z;
+  std::vector<float2*> Xh;
+  float *a = nullptr, *h = nullptr, *out = nullptr, *dout = nullptr;
+  float *dv = nullptr, *dz = nullptr, *dt = nullptr, *mom = nullptr, *part = nullptr, *cky = nullptr, *cky_s = nullptr;
+  float2 *A = nullptr, *Y = nullptr, *dY = nullptr, *tw = nullptr;
+  double* lpart = nullptr;
+  std::vector<void*> owned;
+};
+
+namespace {
+
+template <typename P>
+cudaError_t alloc(bem_fno_s* f, P** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(P));
+  if (e == cudaSuccess) f->owned.push_back(*p);
+  return e;
+}
+
+constexpr int kMaxSamples = 4096;
+constexpr size_t kPersistent = 6;   // parameters, optimiser state and moments come first in owned
+
+void free_acts(bem_fno_s* f) {
+  for (size_t i = kPersistent; i < f->owned.size(); ++i) cudaFree(f->owned[i]);
+  f->owned.resize(std::min<size_t>(f->owned.size(), kPersistent));
+  f->v.clear();
+  f->z.clear();
+  f->Xh.clear();
+  f->capB = f->capN = f->twN = 0;
+}
+
+bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
+  if (B <= f->capB && N <= f->capN && (!train || f->cap_train)) {
+    if (f->twN != N) {
+      k_twiddle_f<<<blocks_for(N), FT, 0, s>>>(f->tw, N);
+      note_launches(1);
+      f->twN = N;
+    }
+    return BEM_OK;
+  }
+  free_acts(f);
+  const int W = f->d.width, m = f->d.modes, L = f->d.layers, H = f->d.hidden;
+  const size_t P = (size_t)N * N;
+  const size_t nm = 2 * (size_t)m * m;
+  const int nv = train ? L + 1 : 2, nz = train ? L : 1;
+  cudaError_t e = cudaSuccess;
+  f->v.resize(nv);
+  f->z.resize(nz);
+  f->Xh.resize(train ? L : 1);
+  for (int i = 0; i < nv && e == cudaSuccess; ++i) e = alloc(f, &f->v[i], (size_t)B * W * P);
+  for (int i = 0; i < nz && e == cudaSuccess; ++i) e = alloc(f, &f->z[i], (size_t)B * W * P);
+  for (size_t i = 0; i < f->Xh.size() && e == cudaSuccess; ++i) e = alloc(f, &f->Xh[i], (size_t)B * W * nm);
+  if (e == cudaSuccess) e = alloc(f, &f->a, (size_t)B * H * P);
+  if (e == cudaSuccess) e = alloc(f, &f->h, (size_t)B * H * P);
+  if (e == cudaSuccess) e = alloc(f, &f->out, (size_t)B * P);
+  if (e == cudaSuccess) e = alloc(f, &f->dout, (size_t)B * P);
+  const size_t big = (size_t)B * std::max(W, H) * P;
+  if (e == cudaSuccess && train) e = alloc(f, &f->dv, big);
+  if (e == cudaSuccess && train) e = alloc(f, &f->dz, big);
+  if (e == cudaSuccess && train) e = alloc(f, &f->dt, big);
+  if (e == cudaSuccess) e = alloc(f, &f->A, (size_t)B * W * N * m);
+  if (e == cudaSuccess) e = alloc(f, &f->Y, (size_t)B * W * nm);
+  if (e == cudaSuccess) e = alloc(f, &f->dY, (size_t)B * W * nm);
+  if (e == cudaSuccess) e = alloc(f, &f->tw, (size_t)N);
+  const size_t nblk = (size_t)B * ((P + FT - 1) / FT);
+  const size_t maxout = (size_t)std::max(W, H) * std::max({W, H, 7}) + std::max(W, H);
+  if (e == cudaSuccess && train) e = alloc(f, &f->part, nblk * maxout);
+  if (e == cudaSuccess) e = alloc(f, &f->lpart, (size_t)4096);
+  if (e == cudaSuccess) e = alloc(f, &f->cky, (size_t)m);
+  if (e == cudaSuccess) e = alloc(f, &f->cky_s, (size_t)m);
+  if (e != cudaSuccess) {
+    free_acts(f);
+    return cuda_fail(e, "cudaMalloc(fno activations)");
+  }
+  f->capB = B;
+  f->capN = N;
+  f->cap_train = train;
+  std::vector<float> c(m), cs(m);
+  for (int k = 0; k < m; ++k) {
+    c[k] = k == 0 ? 1.f : 2.f;
+    cs[k] = c[k] / (float)((double)N * N);
+  }
+  BEM_CUDA_TRY(cudaMemcpyAsync(f->cky, c.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
+  BEM_CUDA_TRY(cudaMemcpyAsync(f->cky_s, cs.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  k_twiddle_f<<<blocks_for(N), FT, 0, s>>>(f->tw, N);
+  note_launches(1);
+  f->twN = N;
+  return BEM_OK;
+}
+
+// pointwise layer dispatch on the (compile-time) input width
+template <bool TRANS, bool ACCUM, bool GELU>
+void pw(const float* X, int cin, const bf16* Wt, const bf16* bias, float* Y, float* Yact, int cout, size_t P, int B,
+        cudaStream_t s) {
+  dim3 grid((unsigned)((P + FT - 1) / FT), B);
+  const size_t sm = (size_t)cout * cin * sizeof(float);
+  switch (cin) {
+    case 1: k_pw<1, TRANS, ACCUM, GELU><<<grid, FT, sm, s>>>(X, Wt, bias, Y, Yact, cout, P); break;
+    case 7: k_pw<7, TRANS, ACCUM, GELU><<<grid, FT, sm, s>>>(X, Wt, bias, Y, Yact, cout, P); break;
+    case 8: k_pw<8, TRANS, ACCUM, GELU><<<grid, FT, sm, s>>>(X, Wt, bias, Y, Yact, cout, P); break;
+    case 16: k_pw<16, TRANS, ACCUM, GELU><<<grid, FT, sm, s>>>(X, Wt, bias, Y, Yact, cout, P); break;
+    case 32: k_pw<32, TRANS, ACCUM, GELU><<<grid, FT, sm, s>>>(X, Wt, bias, Y, Yact, cout, P); break;
+    case 64: k_pw<64, TRANS, ACCUM, GELU><<<grid, FT, sm, s>>>(X, Wt, bias, Y, Yact, cout, P); break;
+    default: break;
+  }
+  note_launches(1);
+}
+
+bool width_ok(int c) { return c == 1 || c == 7 || c == 8 || c == 16 || c == 32 || c == 64; }
+
+void wgrad(const float* dY, int cout, const float* X, int cin, float* gw, float* gb, float* part, size_t P, int B,
+           cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_pw_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid((unsigned)((P + FT - 1) / FT), B);
+  const size_t sm = (size_t)(cout + cin) * FT * sizeof(float);
+  k_pw_wgrad<<<grid, FT, sm, s>>>(dY, X, part, cout, cin, P);
+  const int nblk = (int)(grid.x * grid.y);
+  k_pw_wgrad_sum<<<blocks_for((size_t)cout * cin + cout), FT, 0, s>>>(part, nblk, cout, cin, gw, gb);
+  note_launches(2);
+}
+
+// spectral branch: out (=|+=) idft( R * dft(vin) ), caching dft(vin) in Xh
+void spectral_fwd(bem_fno_s* f, int l, const float* vin, float2* Xh, float* out, int B, int N, cudaStream_t s) {
+  const int W = f->d.width, m = f->d.modes;
+  const size_t bc = (size_t)B * W, nm = 2 * (size_t)m * m;
+  k_dft_y<<<blocks_for(bc * N * m), FT, 0, s>>>(vin, f->A, f->tw, N, m, bc * N);
+  k_dft_x<<<blocks_for(bc * nm), FT, 0, s>>>(f->A, Xh, f->tw, nullptr, N, m, bc);
+  const bf16* Rre = f->wb + f->o_Rre + (size_t)l * W * W * nm;
+  const bf16* Rim = f->wb + f->o_Rim + (size_t)l * W * W * nm;
+  k_mix<<<blocks_for(bc * nm), FT, 0, s>>>(Xh, Rre, Rim, f->Y, W, (int)nm, B);
+  k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
+  k_idft_y<false><<<blocks_for(bc * N * N), FT, 0, s>>>(f->A, out, f->tw, f->cky, 1.f / ((float)N * N), N, m, bc * N);
+  note_launches(5);
+}
+
+bem_status forward(bem_fno_s* f, int B, int N, const float* x, bool train, cudaStream_t s) {
+  const int W = f->d.width, L = f->d.layers, H = f->d.hidden;
+  const size_t P = (size_t)N * N;
+  pw<false, false, false>(x, 7, f->wb + f->o_Pw, f->wb + f->o_Pb, f->v[0], nullptr, W, P, B, s);
+  for (int l = 0; l < L; ++l) {
+    float* vin = train ? f->v[l] : f->v[l & 1];
+    float* z = train ? f->z[l] : f->z[0];
+    float2* Xh = train ? f->Xh[l] : f->Xh[0];
+    spectral_fwd(f, l, vin, Xh, z, B, N, s);
+    const bf16* Ww = f->wb + f->o_Ww + (size_t)l * W * W;
+    const bf16* Wb = f->wb + f->o_Wb + (size_t)l * W;
+    float* vout = train ? f->v[l + 1] : f->v[(l + 1) & 1];
+    if (l < L - 1) {
+      pw<false, true, true>(vin, W, Ww, Wb, z, vout, W, P, B, s);
+    } else {
+      pw<false, true, false>(vin, W, Ww, Wb, z, nullptr, W, P, B, s);
+      BEM_CUDA_TRY(cudaMemcpyAsync(vout, z, (size_t)B * W * P * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  float* vL = train ? f->v[L] : f->v[L & 1];
+  pw<false, false, true>(vL, W, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->a, f->h, H, P, B, s);
+  pw<false, false, false>(f->h, H, f->wb + f->o_Q2w, f->wb + f->o_Q2b, f->out, nullptr, 1, P, B, s);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status backward(bem_fno_s* f, int B, int N, const float* x, const float* target, double* loss, cudaStream_t s) {
+  const int W = f->d.width, m = f->d.modes, L = f->d.layers, H = f->d.hidden;
+  const size_t P = (size_t)N * N, nm = 2 * (size_t)m * m, bc = (size_t)B * W;
+  const int lb = std::min(blocks_for((size_t)B * P), 4096);
+  k_mse<<<lb, FT, 0, s>>>(f->out, target, f->dout, f->lpart, (size_t)B * P);
+  note_launches(1);
+  std::vector<double> lp(lb);
+  BEM_CUDA_TRY(cudaMemcpyAsync(lp.data(), f->lpart, lb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // projection
+  wgrad(f->dout, 1, f->h, H, f->g + f->o_Q2w, f->g + f->o_Q2b, f->part, P, B, s);
+  pw<true, false, false>(f->dout, 1, f->wb + f->o_Q2w, nullptr, f->dt, nullptr, H, P, B, s);   // d_h
+  k_gelu_bwd<<<blocks_for((size_t)B * H * P), FT, 0, s>>>(f->dt, f->a, f->dz, (size_t)B * H * P);   // d_a
+  note_launches(1);
+  wgrad(f->dz, H, f->v[L], W, f->g + f->o_Q1w, f->g + f->o_Q1b, f->part, P, B, s);
+  pw<true, false, false>(f->dz, H, f->wb + f->o_Q1w, nullptr, f->dv, nullptr, W, P, B, s);     // d_v
+  for (int l = L - 1; l >= 0; --l) {
+    const float* dz = f->dv;
+    if (l < L - 1) {
+      k_gelu_bwd<<<blocks_for(bc * P), FT, 0, s>>>(f->dv, f->z[l], f->dz, bc * P);
+      note_launches(1);
+      dz = f->dz;
+    }
+    wgrad(dz, W, f->v[l], W, f->g + f->o_Ww + (size_t)l * W * W, f->g + f->o_Wb + (size_t)l * W, f->part, P, B, s);
+    // pointwise branch of d_vin into dt
+    pw<true, false, false>(dz, W, f->wb + f->o_Ww + (size_t)l * W * W, nullptr, f->dt, nullptr, W, P, B, s);
+    // spectral branch: dY = (c/N^2) dft(dz); dR = sum_b conj(Xh) dY; dXh = sum_o conj(R) dY
+    k_dft_y<<<blocks_for(bc * N * m), FT, 0, s>>>(dz, f->A, f->tw, N, m, bc * N);
+    k_dft_x<<<blocks_for(bc * nm), FT, 0, s>>>(f->A, f->dY, f->tw, f->cky_s, N, m, bc);
+    const bf16* Rre = f->wb + f->o_Rre + (size_t)l * W * W * nm;
+    const bf16* Rim = f->wb + f->o_Rim + (size_t)l * W * W * nm;
+    k_mix_wgrad<<<blocks_for((size_t)W * W * nm), FT, 0, s>>>(f->Xh[l], f->dY, f->g + f->o_Rre + (size_t)l * W * W * nm,
+                                                          f->g + f->o_Rim + (size_t)l * W * W * nm, W, (int)nm, B);
+    k_mix_dgrad<<<blocks_for(bc * nm), FT, 0, s>>>(f->dY, Rre, Rim, f->Y, W, (int)nm, B);
+    // d_vin += Re(sum dXh e^{+i theta}) (adjoint of the forward transform)
+    k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
+    k_idft_y<true><<<blocks_for(bc * N * N), FT, 0, s>>>(f->A, f->dt, f->tw, nullptr, 1.f, N, m, bc * N);
+    note_launches(6);
+    std::swap(f->dv, f->dt);
+  }
+  wgrad(f->dv, W, x, 7, f->g + f->o_Pw, f->g + f->o_Pb, f->part, P, B, s);
+  BEM_CUDA_TRY(cudaGetLastError());
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  double sum = 0.0;
+  for (double v : lp) sum += v;
+  *loss = sum / (double)((size_t)B * P);
+  return BEM_OK;
+}
+
+bool is_dev(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+bem_status bem_fno_create(const bem_fno_desc* desc, bem_fno* out) {
+  if (desc == nullptr || out == nullptr) { set_error("NULL argument"); return BEM_EINVAL; }
+  *out = nullptr;
+  if (!width_ok(desc->width) || !width_ok(desc->hidden) || desc->modes < 1 || desc->layers < 1 ||
+      desc->layers > 16) {
+    set_error("FNO widths must be one of 1, 7, 8, 16, 32, 64; modes >= 1; 1 <= layers <= 16");
+    return BEM_EINVAL;
+  }
+  bem_fno_s* f = new bem_fno_s();
+  f->d = *desc;
+  cudaGetDevice(&f->dev);
+  const size_t W = desc->width, m = desc->modes, L = desc->layers, H = desc->hidden;
+  const size_t nm = 2 * m * m;
+  size_t off = 0;
+  f->o_Pw = off; off += W * 7;
+  f->o_Pb = off; off += W;
+  f->o_Rre = off; off += L * W * W * nm;
+  f->o_Rim = off; off += L * W * W * nm;
+  f->o_Ww = off; off += L * W * W;
+  f->o_Wb = off; off += L * W;
+  f->o_Q1w = off; off += H * W;
+  f->o_Q1b = off; off += H;
+  f->o_Q2w = off; off += H;
+  f->o_Q2b = off; off += 1;
+  f->P = off;
+  cudaError_t e = alloc(f, &f->w, f->P);
+  if (e == cudaSuccess) e = alloc(f, &f->wb, f->P);
+  if (e == cudaSuccess) e = alloc(f, &f->g, f->P);
+  if (e == cudaSuccess) e = alloc(f, &f->m1, f->P);
+  if (e == cudaSuccess) e = alloc(f, &f->m2, f->P);
+  if (e == cudaSuccess) e = alloc(f, &f->mom, (size_t)2 * kMaxSamples);
+  if (e != cudaSuccess) {
+    for (void* p : f->owned) cudaFree(p);
+    delete f;
+    return cuda_fail(e, "cudaMalloc(fno parameters)");
+  }
+  cudaMemset(f->w, 0, f->P * sizeof(float));
+  cudaMemset(f->wb, 0, f->P * sizeof(bf16));
+  cudaMemset(f->g, 0, f->P * sizeof(float));
+  cudaMemset(f->m1, 0, f->P * sizeof(float));
+  cudaMemset(f->m2, 0, f->P * sizeof(float));
+  *out = f;
+  return BEM_OK;
+}
+
+bem_status bem_fno_destroy(bem_fno f) {
+  if (f == nullptr) return BEM_OK;
+  cudaDeviceSynchronize();
+  for (void* p : f->owned) cudaFree(p);
+  delete f;
+  return BEM_OK;
+}
+
+int64_t bem_fno_param_count(bem_fno f) { return f == nullptr ? -1 : (int64_t)f->P; }
+
+bem_status bem_fno_set_params(bem_fno f, const float* w, int64_t count, void* cuda_stream) {
+  if (f == nullptr || w == nullptr || count != (int64_t)f->P) { set_error("bad parameter vector"); return BEM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  BEM_CUDA_TRY(cudaMemcpyAsync(f->w, w, f->P * sizeof(float), cudaMemcpyDefault, s));
+  k_to_bf16<<<blocks_for(f->P), FT, 0, s>>>(f->w, f->wb, f->P);
+  note_launches(1);
+  BEM_CUDA_TRY(cudaMemsetAsync(f->m1, 0, f->P * sizeof(float), s));
+  BEM_CUDA_TRY(cudaMemsetAsync(f->m2, 0, f->P * sizeof(float), s));
+  f->step = 0;
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_fno_get_params(bem_fno f, float* w, int64_t count, int32_t rounded, void* cuda_stream) {
+  if (f == nullptr || w == nullptr || count != (int64_t)f->P) { set_error("bad parameter vector"); return BEM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (rounded) {
+    // the bf16 values the kernels use, widened to float (staged through the gradient buffer)
+    k_bf16_to_f32<<<blocks_for(f->P), FT, 0, s>>>(f->wb, f->g, f->P);
+    note_launches(1);
+    BEM_CUDA_TRY(cudaMemcpyAsync(w, f->g, f->P * sizeof(float), cudaMemcpyDefault, s));
+  } else {
+    BEM_CUDA_TRY(cudaMemcpyAsync(w, f->w, f->P * sizeof(float), cudaMemcpyDefault, s));
+  }
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* heights, const double* params, float* x,
+                            void* cuda_stream) {
+  if (f == nullptr || heights == nullptr || params == nullptr || x == nullptr || B < 1 || N < 2) {
+    set_error("invalid FNO feature arguments");
+    return BEM_EINVAL;
+  }
+  if (!is_dev(heights) || !is_dev(params) || !is_dev(x)) { set_error("FNO arrays must be device arrays"); return BEM_EINVAL; }
+  if (B > kMaxSamples) { set_error("at most 4096 samples per feature call"); return BEM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t P = (size_t)N * N;
+  k_fno_moments<<<B, FT, 0, s>>>(heights, f->mom, P);
+  k_fno_features<<<blocks_for((size_t)B * P), FT, 0, s>>>(heights, f->mom, params, x, N, B);
+  note_launches(2);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, float* out, void* cuda_stream) {
+  if (f == nullptr || x == nullptr || out == nullptr || B < 1 || N < 2 * f->d.modes) {
+    set_error("invalid FNO forward arguments (N must be at least twice the retained modes)");
+    return BEM_EINVAL;
+  }
+  if (!is_dev(x) || !is_dev(out)) { set_error("FNO arrays must be device arrays"); return BEM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  bem_status st = ensure(f, B, N, false || (f->cap_train && B <= f->capB && N <= f->capN), s);
+  if (st != BEM_OK) return st;
+  st = forward(f, B, N, x, f->cap_train, s);
+  if (st != BEM_OK) return st;
+  BEM_CUDA_TRY(cudaMemcpyAsync(out, f->out, (size_t)B * N * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return BEM_OK;
+}
+
+bem_status bem_fno_gradients(bem_fno f, int32_t B, int32_t N, const float* x, const float* target, float* grad,
+                             double* loss, void* cuda_stream) {
+  if (f == nullptr || x == nullptr || target == nullptr || loss == nullptr || B < 1 || N < 2 * f->d.modes) {
+    set_error("invalid FNO gradient arguments");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  bem_status st = ensure(f, B, N, true, s);
+  if (st != BEM_OK) return st;
+  st = forward(f, B, N, x, true, s);
+  if (st != BEM_OK) return st;
+  st = backward(f, B, N, x, target, loss, s);
+  if (st != BEM_OK) return st;
+  if (grad != nullptr) {
+    BEM_CUDA_TRY(cudaMemcpyAsync(grad, f->g, f->P * sizeof(float), cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return BEM_OK;
+}
+
+bem_status bem_fno_train_step(bem_fno f, int32_t B, int32_t N, const float* x, const float* target, float lr,
+                              double* loss, void* cuda_stream) {
+  bem_status st = bem_fno_gradients(f, B, N, x, target, nullptr, loss, cuda_stream);
+  if (st != BEM_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  f->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f / (1.f - powf(b1, (float)f->step)), c2 = 1.f / (1.f - powf(b2, (float)f->step));
+  k_adam<<<blocks_for(f->P), FT, 0, s>>>(f->w, f->g, f->m1, f->m2, f->wb, f->P, lr, b1, b2, c1, c2, 1e-8f);
+  note_launches(1);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status bem_fno_pressure(bem_fno f, int32_t B, int32_t N, const float* out, const double* pbar, float* p,
+                            void* cuda_stream) {
+  if (f == nullptr || out == nullptr || pbar == nullptr || p == nullptr || B < 1) {
+    set_error("invalid FNO pressure arguments");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  k_fno_pressure<<<blocks_for((size_t)B * N * N), FT, 0, s>>>(out, pbar, p, (size_t)N * N, B);
+  note_launches(1);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status bem_fno_target(bem_fno f, int32_t B, int32_t N, const float* p, const double* pbar, float* q,
+                          void* cuda_stream) {
+  if (f == nullptr || p == nullptr || pbar == nullptr || q == nullptr || B < 1) {
+    set_error("invalid FNO target arguments");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  k_fno_target<<<blocks_for((size_t)B * N * N), FT, 0, s>>>(p, pbar, q, (size_t)N * N, B);
+  note_launches(1);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""Learned warm start: solver-generated training data, training, prediction.
+
+Orchestration only: every numerical step runs in libbem.so (contact solves, feature
+construction, network forward/backward/Adam, target and pressure scaling); this
+module moves device tensors between those calls and picks minibatches.
+
+The network predicts q = p / pbar (pbar = F / L^2, the mean pressure) from the height
+map and the layer parameters; the warm start handed to the solver is
+p_init = pbar max(q, 0), which the force-controlled solve then rescales to F exactly.
+"""
+import numpy as np
+import torch
+
+from . import bem, inputs
+
+
+def instance_tensors(insts, device):
+    """Stacks same-size instances: heights [B, N, N] float32, params [B, 4] float64
+    (h/delta, E1/E2, nu1, nu2), pbar [B] float64 — all on the device."""
+    N = insts[0]["N"]
+    assert all(i["N"] == N for i in insts)
+    heights = torch.tensor(np.stack([i["height"] for i in insts]), dtype=torch.float32, device=device)
+    params = torch.tensor([[i["h"] / i["delta"], i["E1"] / i["E2"], i["nu1"], i["nu2"]] for i in insts],
+                          dtype=torch.float64, device=device)
+    pbar = torch.tensor([i["force"] / (i["N"] * i["delta"]) ** 2 for i in insts], dtype=torch.float64,
+                        device=device)
+    return heights, params, pbar
+
+
+def solve_all(insts, heights, p_init=None, tol=1e-8, max_iter=5000, stream=None):
+    """Solves every instance (force control, float) with one batched call; returns
+    (pressures [B, N, N], results)."""
+    ks = [bem.Kernel(i["N"], i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"], precision="fp32")
+          for i in insts]
+    outs = torch.empty_like(heights)
+    probs = [bem.make_problem(heights[b], bem.BEM_CTRL_FORCE, insts[b]["force"], tol=tol, max_iter=max_iter,
+                              p_init=None if p_init is None else p_init[b]) for b in range(len(insts))]
+    st, res = bem.bem_solve_batch([k.handle for k in ks], probs, [outs[b] for b in range(len(insts))],
+                                  stream=stream)
+    for k in ks:
+        k.close()
+    return outs, res
+
+
+def make_dataset(fno, insts, device, tol=1e-8):
+    """Features x [B, 7, N, N] and targets q [B, N, N] from solver solutions."""
+    heights, params, pbar = instance_tensors(insts, device)
+    p, res = solve_all(insts, heights, tol=tol)
+    B, N = heights.shape[0], heights.shape[-1]
+    x = torch.empty((B, 7, N, N), dtype=torch.float32, device=device)
+    fno.features(B, N, heights, params, x)
+    q = torch.empty_like(heights)
+    fno.target(B, N, p, pbar, q)
+    torch.cuda.synchronize(device)
+    return x, q, res
+
+
+def train(fno, x, q, steps, batch, lr, seed=0, lr_final=None):
+    """Adam on minibatches drawn without replacement per epoch; returns the losses.
+    The learning rate decays geometrically to lr_final (if given)."""
+    rng = np.random.default_rng(seed)
+    B, N = x.shape[0], x.shape[-1]
+    losses = []
+    order = rng.permutation(B)
+    pos = 0
+    for s in range(steps):
+        if pos + batch > B:
+            order = rng.permutation(B)
+            pos = 0
+        idx = torch.as_tensor(order[pos:pos + batch], device=x.device)
+        pos += batch
+        xb = x.index_select(0, idx).contiguous()
+        qb = q.index_select(0, idx).contiguous()
+        rate = lr if lr_final is None else lr * (lr_final / lr) ** (s / max(steps - 1, 1))
+        losses.append(fno.train_step(batch, N, xb, qb, rate))
+    return losses
+
+
+def predict(fno, heights, params, pbar):
+    """Warm-start pressures p_init [B, N, N] for stacked instances."""
+    B, N = heights.shape[0], heights.shape[-1]
+    x = torch.empty((B, 7, N, N), dtype=torch.float32, device=heights.device)
+    fno.features(B, N, heights, params, x)
+    out = torch.empty_like(heights)
+    p = torch.empty_like(heights)
+    for b in range(B):
+        fno.forward(1, N, x[b:b + 1], out[b:b + 1])
+    fno.pressure(B, N, out, pbar, p)
+    return p
+
+
+def default_instances(count, N, seed0):
+    """Rough-surface batch-workload instances at one grid size."""
+    return [inputs.batch_instance(seed0 + i, sizes=(N,)) for i in range(count)]

@@ -1,0 +1,130 @@
+"""GPU warm-start network: forward and gradients against the FP64 oracle network
+(same bfloat16-rounded weights on both sides, float accumulation on the GPU), and
+what the trained network gains over the cold start of the same solver."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fno as ofno
+from paper_1807_01885_gb300 import bem, inputs, warmstart
+
+pytestmark = pytest.mark.gpu
+
+
+def flatten(P):
+    keys = ["P_w", "P_b", "R_re", "R_im", "W_w", "W_b", "Q1_w", "Q1_b", "Q2_w", "Q2_b"]
+    return np.concatenate([P[k].reshape(-1) for k in keys]), keys
+
+
+def unflatten(vec, like):
+    out, off = {}, 0
+    for k in ["P_w", "P_b", "R_re", "R_im", "W_w", "W_b", "Q1_w", "Q1_b", "Q2_w", "Q2_b"]:
+        n = like[k].size
+        out[k] = vec[off:off + n].reshape(like[k].shape).astype(np.float64)
+        off += n
+    assert off == vec.size
+    return out
+
+
+def setup(cuda, W, m, L, H, seed):
+    rng = np.random.default_rng(seed)
+    P = ofno.init_params(rng, 7, W, m, L, H)
+    for k in P:
+        P[k] = P[k] + 0.05 * rng.standard_normal(P[k].shape)
+    net = bem.Fno(width=W, modes=m, layers=L, hidden=H)
+    vec, _ = flatten(P)
+    assert vec.size == net.count
+    net.set_params(torch.tensor(vec, dtype=torch.float32, device=cuda))
+    rounded = torch.empty(net.count, dtype=torch.float32, device=cuda)
+    net.get_params(rounded, rounded=True)
+    return net, unflatten(rounded.cpu().numpy(), P)
+
+
+@pytest.mark.parametrize("W,m,L,H,B,N", [(8, 3, 2, 16, 2, 16), (32, 16, 4, 64, 1, 32)])
+def test_forward_matches_oracle(cuda, W, m, L, H, B, N):
+    net, P = setup(cuda, W, m, L, H, seed=W)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((B, 7, N, N)).astype(np.float32)
+    out = torch.empty((B, N, N), dtype=torch.float32, device=cuda)
+    net.forward(B, N, torch.tensor(x, device=cuda), out)
+    ref, _ = ofno.forward(P, x.astype(np.float64), m)
+    got = out.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-5
+    net.close()
+
+
+def test_gradients_match_oracle(cuda):
+    W, m, L, H, B, N = 8, 3, 2, 16, 2, 16
+    net, P = setup(cuda, W, m, L, H, seed=3)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((B, 7, N, N)).astype(np.float32)
+    t = rng.standard_normal((B, N, N)).astype(np.float32)
+    g = torch.empty(net.count, dtype=torch.float32, device=cuda)
+    loss = net.gradients(B, N, torch.tensor(x, device=cuda), torch.tensor(t, device=cuda), g)
+    out, cache = ofno.forward(P, x.astype(np.float64), m)
+    assert loss == pytest.approx(ofno.loss(out, t.astype(np.float64)), rel=1e-5)
+    G = ofno.backward(P, cache, out, t.astype(np.float64), m)
+    got = unflatten(g.cpu().numpy(), P)
+    for k in G:
+        err = np.linalg.norm(got[k] - G[k]) / max(np.linalg.norm(G[k]), 1e-30)
+        assert err < 1e-4, (k, err)
+    net.close()
+
+
+def test_features(cuda):
+    N, B = 32, 3
+    insts = [inputs.batch_instance(20260300 + i, sizes=(N,)) for i in range(B)]
+    heights, params, pbar = warmstart.instance_tensors(insts, cuda)
+    net = bem.Fno(width=8, modes=3, layers=1, hidden=8)
+    x = torch.empty((B, 7, N, N), dtype=torch.float32, device=cuda)
+    net.features(B, N, heights, params, x)
+    xc = x.cpu().numpy()
+    for b, inst in enumerate(insts):
+        f = inst["height"]
+        np.testing.assert_allclose(xc[b, 0], (f - f.mean()) / f.std(), atol=1e-4)
+        assert xc[b, 1, 0, 0] == pytest.approx(np.log(inst["h"] / inst["delta"]) / np.log(200), rel=1e-6)
+        assert xc[b, 2, 3, 4] == pytest.approx(np.log(inst["E1"] / inst["E2"]) / np.log(20), rel=1e-6)
+        assert xc[b, 3, 5, 5] == pytest.approx(inst["nu1"], rel=1e-6)
+        assert xc[b, 5, 0, 2] == pytest.approx(2.5 / N) and xc[b, 6, 2, 0] == pytest.approx(2.5 / N)
+    net.close()
+
+
+def test_training_reduces_loss(cuda):
+    net, _ = setup(cuda, 16, 6, 2, 16, seed=5)
+    rng = np.random.default_rng(6)
+    B, N = 16, 32
+    x = torch.tensor(rng.standard_normal((B, 7, N, N)).astype(np.float32), device=cuda)
+    q = torch.tanh(x[:, 0] + 0.5 * x[:, 5]).contiguous()
+    losses = warmstart.train(net, x, q, steps=150, batch=4, lr=3e-3)
+    assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
+    net.close()
+
+
+def test_warm_start_gain(cuda):
+    """Trained on solver solutions at N = 64, the network's pressure field seeds the
+    float solve of unseen instances: the solutions agree with the cold solves and
+    the CG iteration count drops."""
+    N = 64
+    net = bem.Fno(width=32, modes=12, layers=4, hidden=64)
+    rng = np.random.default_rng(7)
+    P = ofno.init_params(rng, 7, 32, 12, 4, 64)
+    vec, _ = flatten(P)
+    net.set_params(torch.tensor(vec, dtype=torch.float32, device=cuda))
+    train_insts = warmstart.default_instances(160, N, 30000000)
+    x, q, _ = warmstart.make_dataset(net, train_insts, cuda)
+    losses = warmstart.train(net, x, q, steps=600, batch=8, lr=2e-3, lr_final=2e-4)
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    test_insts = warmstart.default_instances(12, N, 40000000)
+    heights, params, pbar = warmstart.instance_tensors(test_insts, cuda)
+    p_cold, r_cold = warmstart.solve_all(test_insts, heights)
+    p_init = warmstart.predict(net, heights, params, pbar)
+    p_warm, r_warm = warmstart.solve_all(test_insts, heights, p_init=p_init)
+    it_cold = np.array([r["iters"] for r in r_cold])
+    it_warm = np.array([r["iters"] for r in r_warm])
+    assert all(r["status"] == 0 for r in r_cold + r_warm)
+    for b in range(len(test_insts)):
+        a, c = p_warm[b].double(), p_cold[b].double()
+        assert float((a - c).norm() / c.norm()) < 2e-4
+    print(f"warm-start iterations {it_warm.mean():.1f} vs cold {it_cold.mean():.1f}")
+    assert it_warm.mean() < it_cold.mean()
+    net.close()
