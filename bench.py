@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=48, help="instances of the batch workload (0: skip)")
+    ap.add_argument("--warmstart", type=int, default=512,
+                    help="training solutions for the learned warm start (0: skip)")
     return ap.parse_args()
 
 
@@ -205,6 +207,69 @@ def batch_bench(torch, dev, bem, inputs, n_inst):
             "seeds": f"{BATCH_SEED0}..{BATCH_SEED0 + n_inst - 1}"}
 
 
+WS_TRAIN_SEED0 = 30000000
+WS_TEST_SEED0 = 40000000
+
+
+def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
+    """Learned warm start: the network is trained here on n_train solver solutions at
+    N = 256 (rough-surface workload), then seeds FP32 solves at N = 2048 of n_test
+    held-out instances; cold and seeded solves to 1e-8 are timed on one stream."""
+    from paper_1807_01885_gb300 import warmstart
+    net = bem.Fno(width=32, modes=16, layers=4, hidden=64)
+    rng = np.random.default_rng(7)
+    cnt = net.count
+    init = np.concatenate([rng.standard_normal(32 * 7) / np.sqrt(7), np.zeros(32),
+                           rng.random(2 * 4 * 32 * 32 * 32 * 16) / (32 * 32),
+                           rng.standard_normal(4 * 32 * 32) / np.sqrt(32), np.zeros(4 * 32),
+                           rng.standard_normal(64 * 32) / np.sqrt(32), np.zeros(64),
+                           rng.standard_normal(64) / 8.0, np.zeros(1)]).astype(np.float32)
+    assert init.size == cnt
+    net.set_params(torch.tensor(init, device=dev))
+    insts = warmstart.default_instances(n_train, 256, WS_TRAIN_SEED0)
+    t0 = time.perf_counter()
+    xs, qs = [], []
+    for c in range(0, n_train, 128):
+        x, q, _ = warmstart.make_dataset(net, insts[c:c + 128], dev)
+        xs.append(x)
+        qs.append(q)
+    x, q = torch.cat(xs), torch.cat(qs)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = warmstart.train(net, x, q, steps=steps, batch=8, lr=2e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, q, xs, qs
+    test = warmstart.default_instances(n_test, N_GRID, WS_TEST_SEED0)
+    heights, params, pbar = warmstart.instance_tensors(test, dev)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        warmstart.solve_all(test, heights, stream=s)                     # graph capture, warm caches
+        s.synchronize()
+        t0 = time.perf_counter()
+        _, r_cold = warmstart.solve_all(test, heights, stream=s)
+        s.synchronize()
+        t_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        p_init = warmstart.predict(net, heights, params, pbar)
+        torch.cuda.synchronize()
+        t_pred = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, r_warm = warmstart.solve_all(test, heights, p_init=p_init, stream=s)
+        s.synchronize()
+        t_warm = time.perf_counter() - t0
+    net.close()
+    return {"train_samples": n_train, "train_N": 256, "train_steps": steps, "batch": 8,
+            "data_s": t_data, "train_s": t_train,
+            "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
+            "test_N": N_GRID, "test_instances": n_test, "test_seeds": f"{WS_TEST_SEED0}..{WS_TEST_SEED0 + n_test - 1}",
+            "cold_ms_per_solve": 1000 * t_cold / n_test, "inference_ms_per_solve": 1000 * t_pred / n_test,
+            "warm_ms_per_solve": 1000 * t_warm / n_test,
+            "warm_plus_inference_ms_per_solve": 1000 * (t_warm + t_pred) / n_test,
+            "cold_iters": [r["iters"] for r in r_cold], "warm_iters": [r["iters"] for r in r_warm],
+            "all_converged": all(r["status"] == 0 for r in r_cold + r_warm)}
+
+
 def cpu_oracle_matvecs(seconds_hint=True):
     """One N = 2048 product of the FP64 oracle (its own radix-2 FFT), timed."""
     from oracle import operator
@@ -253,22 +318,22 @@ def run_ours(args):
         build.build()
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
+    # a non-default stream: solves replay their captured CG iteration graphs
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     insts = make_instances(torch, dev, bem, inputs)
 
     def step(i):
         c = insts[i % N_INST]
-        _, res = c["kernel"].solve(c["f"], "force", c["inst"]["force"], tol=TOL, max_iter=5000, p_out=c["p"])
+        _, res = c["kernel"].solve(c["f"], "force", c["inst"]["force"], tol=TOL, max_iter=5000, p_out=c["p"],
+                                   stream=stream)
         if res["status"] != 0:
             raise RuntimeError(f"solve failed: {res}")
         return res
 
     for i in range(args.warmup):
         step(i)
-    for c in insts:
-        bem.bem_set_pass_timing(c["kernel"].handle, True)
-        bem.bem_pass_timing(c["kernel"].handle, reset=True)
-    # timed region
+    # timed region (pass timing off: nothing but the solves runs in it)
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
@@ -283,13 +348,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = bem.bem_launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    pass_ms, pass_n = [0.0, 0.0, 0.0], [0, 0, 0]
-    for c in insts:
-        m_, n_ = bem.bem_pass_timing(c["kernel"].handle, reset=True)
-        bem.bem_set_pass_timing(c["kernel"].handle, False)
-        pass_ms = [a + b for a, b in zip(pass_ms, m_)]
-        pass_n = [a + b for a, b in zip(pass_n, n_)]
-    pass_mean = [pass_ms[i] / max(pass_n[i], 1) for i in range(3)]
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -303,6 +361,23 @@ def run_ours(args):
         t = tt
     ms_max, mv_all = float(t[0]), float(t[1])
     value = mv_all / (ms_max / 1000.0)
+
+    # second timed region, same steps with the library recording CUDA events around
+    # every pass on the launching stream (plain launches): the per-pass durations
+    for c in insts:
+        bem.bem_set_pass_timing(c["kernel"].handle, True)
+        bem.bem_pass_timing(c["kernel"].handle, reset=True)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        step(i)
+    torch.cuda.synchronize()
+    pass_ms, pass_n = [0.0, 0.0, 0.0], [0, 0, 0]
+    for c in insts:
+        m_, n_ = bem.bem_pass_timing(c["kernel"].handle, reset=True)
+        bem.bem_set_pass_timing(c["kernel"].handle, False)
+        pass_ms = [a + b for a, b in zip(pass_ms, m_)]
+        pass_n = [a + b for a, b in zip(pass_n, n_)]
+    pass_mean = [pass_ms[i] / max(pass_n[i], 1) for i in range(3)]
 
     # matvec-only throughput: 8 distinct inputs and outputs (268 MB > L2)
     k0 = insts[0]["kernel"]
@@ -338,7 +413,7 @@ def run_ours(args):
     for i in range(max(1, args.steps)):
         c = insts[i % N_INST]
         fh, ph = hosts[i % N_INST]
-        _, res = c["kernel"].solve(fh, "force", c["inst"]["force"], tol=TOL, max_iter=5000, p_out=ph)
+        _, res = c["kernel"].solve(fh, "force", c["inst"]["force"], tol=TOL, max_iter=5000, p_out=ph, stream=stream)
         e2e_mv += res["matvecs"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -362,6 +437,7 @@ def run_ours(args):
         "matvec_only": {"value": 1000.0 / mv_ms, "unit": UNIT, "ms_per_matvec": mv_ms,
                         "alg_bytes": sum(rb), "gbs": sum(rb) / (mv_ms * 1e-3) / 1e9},
         "passes_ms_mean": dict(zip(names, pass_mean)),
+        "passes_timing_region": "a second run of the same steps with CUDA events around every pass",
         "passes_launches": dict(zip(names, pass_n)),
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm,
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
@@ -375,6 +451,8 @@ def run_ours(args):
     }
     if args.batch > 0:
         line["batch"] = batch_bench(torch, dev, bem, inputs, args.batch)
+    if args.warmstart > 0:
+        line["warm_start"] = warm_start_bench(torch, dev, bem, args.warmstart, 1500, 2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt = cpu_oracle_matvecs()
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",

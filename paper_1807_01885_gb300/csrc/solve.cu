@@ -116,13 +116,15 @@ __global__ void k_init_apply(const T* __restrict__ f, const T* __restrict__ q, c
   }
 }
 
-// Refresh of the gap after the contact set changed: g = s u + f - d, p *= s, where
-// u = K p was computed from the pressure before the pending load rescale s.
+// Correction of the gap after the contact set changed: the update moved p by
+// -tau t plus a sparse change dp (cells projected to 0 or re-activated), stored in x;
+// with u = K dp the gap becomes g + u, which keeps g a recursively updated residual.
+// Then the pending load rescale: g = s (g + u) + (s - 1)(d - f), p *= s.
 template <typename T>
 __global__ void k_gap(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ p, T* __restrict__ g,
                       const SolveState* st, size_t n) {
   if (st->done || !st->refresh) return;
-  const T s = (T)st->scale;
+  const T s = (T)st->scale, s1 = (T)(st->scale - 1.0);
   const double d = st->d;
   const T dT = (T)d;
   VEC_LOOP(i4, n) {
@@ -130,13 +132,31 @@ __global__ void k_gap(const T* __restrict__ u, const T* __restrict__ f, T* __res
     ld4(u, i4, uv);
     ld4(f, i4, fv);
     ld4(p, i4, pv);
+    ld4(g, i4, gv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      gv[e] = s * uv[e] + (fv[e] - dT);
+      gv[e] = s * (gv[e] + uv[e]) + s1 * (dT - fv[e]);
       pv[e] = s * pv[e];
     }
     st4(g, i4, gv);
     st4(p, i4, pv);
+  }
+}
+
+// Start values for a warm or uniform start: g = f - d (the gap of p = 0) and dp = p,
+// so that the first correction gives g = K p + f - d.
+template <typename T>
+__global__ void k_init_gap(const T* __restrict__ f, const T* __restrict__ p, T* __restrict__ g, T* __restrict__ dp,
+                           const SolveState* st, size_t n) {
+  const T dT = (T)st->d;
+  VEC_LOOP(i4, n) {
+    T fv[4], pv[4], gv[4];
+    ld4(f, i4, fv);
+    ld4(p, i4, pv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gv[e] = fv[e] - dT;
+    st4(g, i4, gv);
+    st4(dp, i4, pv);
   }
 }
 
@@ -277,7 +297,7 @@ __global__ void k_pk_rt(const T* __restrict__ p, const T* __restrict__ g, const 
 // negative gap re-enter with p = -tau g; g -= tau K t.
 template <typename T>
 __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
-                            double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+                            T* __restrict__ dp, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   const T tau = (T)st->tau;
   // Rounding-noise thresholds (float path only): a re-activation needs a gap below
@@ -287,7 +307,7 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
   const T gthr = -noise * (T)st->uscale, pthr = -noise * (T)st->pscale;
   Acc<T> asum, nneg, nol;
   VEC_LOOP(i4, n) {
-    T pv[4], gv[4], tv[4], rv[4];
+    T pv[4], gv[4], tv[4], rv[4], dv[4];
     ld4(p, i4, pv);
     ld4(g, i4, gv);
     ld4(t, i4, tv);
@@ -295,25 +315,29 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const T pi = pv[e], gi = gv[e];
-      T pn;
+      T pn, dpn = (T)0;
       if (pi > (T)0) {
         pn = pi - tau * tv[e];
         if (pn < (T)0) {
           if (pn < pthr) nneg.add((T)1);
+          dpn = -pn;          // the projection moves p from pn to 0
           pn = (T)0;
         }
       } else if (gi < gthr) {
         pn = -tau * gi;
+        dpn = pn;             // re-activation: p moves from 0 to pn
         nol.add((T)1);
       } else {
         pn = (T)0;
       }
       pv[e] = pn;
+      dv[e] = dpn;
       gv[e] = gi - tau * rv[e];
       asum.add(pn);
     }
     st4(p, i4, pv);
     st4(g, i4, gv);
+    st4(dp, i4, dv);
   }
   Acc<T> v[3] = {asum, nneg, nol};
   double tot[3];
@@ -644,10 +668,12 @@ bem_status pk_setup(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cu
   if (pinit != nullptr) {
     if (pinit != v.p) BEM_CUDA_TRY(cudaMemcpyAsync(v.p, pinit, c.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     k_init_clamp<T><<<c.rb, NTHREADS, 0, s>>>(v.p, part, tk, st, c.n);
-    note_launches(1);
+    k_init_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.p, v.g, v.x, st, c.n);
+    note_launches(2);
   } else if (force) {
     k_fill<T><<<c.eb, NTHREADS, 0, s>>>(v.p, prob->target / (delta2 * (double)c.n), c.n);
-    note_launches(1);
+    k_init_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.p, v.g, v.x, st, c.n);
+    note_launches(2);
   } else {
     k_init_q<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.x, prob->target, c.n);
     note_launches(1);
@@ -673,13 +699,13 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
   double* part = k->ws.partials;
   unsigned int* tk = k->ws.ticket;
   for (int it = 0; it < CHUNK; ++it) {
-    launch_matvec<T>(k, v.p, v.u, s, &st->mv_p_on);
+    launch_matvec<T>(k, v.x, v.u, s, &st->mv_p_on);
     k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, st, c.n);
     k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, part, tk, st, c.n);
     k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
     launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
     k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
-    k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
+    k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, part, tk, st, c.n);
     note_launches(5);
   }
 }

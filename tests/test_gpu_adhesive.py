@@ -1,0 +1,97 @@
+"""Adhesive contact on the GPU against the paper's asymptotic solutions (Sec. 3).
+
+Each case runs the displacement-controlled procedure of Sec. 2 with the detachment
+stress of Eq. (12); the results must approach the closed forms within the
+discretisation error of the grid used (the paper itself claims only close agreement
+for Figs. 3 and 5).  Also: resuming a saved ramp repeats the same trajectory."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import analytic, kernel as okernel
+from paper_1807_01885_gb300 import bem, inputs, ramp
+
+pytestmark = pytest.mark.gpu
+
+
+def test_jkr_homogeneous_pull_off_force(cuda):
+    """E1 = E2: the minimum force of the pull-off ramp approaches -(3/2) pi R dgamma
+    (JKR, Eqs. 22/23 at epsilon = 0); jump-off radius 16 cells, force minimum at 33."""
+    N, R, E, nu = 256, 1.0, 1.0, 0.3
+    delta = 1.0 / N
+    Es = okernel.e_star(E, nu)
+    a_d = 16 * delta
+    dg = a_d ** 3 * 8 * Es / (np.pi * R * R)
+    a_F = 9 ** (1 / 3) * a_d
+    f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda)
+    d_max = (1.3 * a_F) ** 2 / R
+    d_jump = analytic.jkr_jump_off(R, Es, dg)[2]
+    depths = ramp.depth_schedule(d_max, 1.2 * d_jump, 10, 90)
+    with bem.Kernel(N, delta, np.inf, E, nu, E, nu) as k:
+        out = ramp.run(k, f, depths, dg, tol=1e-10)
+    assert all(r["status"] == 0 for r in out)
+    Fmin = min(r["force"] for r in out)
+    assert Fmin / analytic.jkr_pull_off_force(R, dg) == pytest.approx(1.0, abs=0.06)
+    assert out[-1]["n_contact"] == 0
+
+
+def test_thin_layer_flat_punch_critical_point(cuda):
+    """Fig. 3: flat punch, a = 50 h, E2/E1 = 1e5, nu = 0.3; the force-displacement line
+    ends at the critical point of Eq. (16), (F/|Fc|, d/|dc|) -> (-1, -1).  delta = h/4."""
+    E1, nu, dg = 2e9, 0.3, 100.0
+    h = 1e-4
+    a = 50 * h
+    delta = h / 4
+    N = 512
+    f = torch.tensor(inputs.flat_punch_height(N, delta, a), device=cuda)
+    dc, Fc = analytic.thin_layer_flat_punch_critical(a, h, E1, nu, dg)
+    depths = ramp.depth_schedule(0.2 * abs(dc), -1.3 * abs(dc), 3, 75)
+    with bem.Kernel(N, delta, h, E1, nu, 1e5 * E1, nu) as k:
+        out = ramp.run(k, f, depths, dg, tol=1e-9)
+    assert all(r["status"] == 0 for r in out)
+    attached = [r for r in out if r["n_contact"] > 0 and r["d"] < 0]
+    last = attached[-1]
+    # the step grid is 1.9 % of |dc|; the critical point is passed within one step
+    assert last["d"] / abs(dc) == pytest.approx(-1.0, abs=0.06)
+    assert min(r["force"] for r in attached) / abs(Fc) == pytest.approx(-1.0, abs=0.08)
+    assert out[-1]["n_contact"] == 0
+
+
+def test_thin_layer_sphere_fig5_alpha15(cuda):
+    """Fig. 5, alpha = 15 (a >> h): rigid base, E1 = 1e9, nu1 = 0.3, h = 2 mm,
+    dgamma = 100; the pull-off force approaches F_crit = -2 pi R dgamma (Eqs. 19-21)."""
+    E1, nu, h, dg = 1e9, 0.3, 2e-3, 100.0
+    R = 15.0 * np.sqrt(okernel.e_star(E1, nu) * h ** 3 / (2 * dg))
+    d_crit, a_crit, F_crit = analytic.thin_layer_sphere_critical(R, h, E1, nu, dg)
+    N = 512
+    L = 4 * 1.5 * a_crit
+    delta = L / N
+    assert delta < h / 2
+    f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda)
+    a_max = 1.5 * a_crit
+    d_max = analytic.thin_layer_sphere(a_max, R, h, E1, nu, 0.0)[1]
+    depths = ramp.depth_schedule(d_max, 1.3 * d_crit, 8, 80)
+    with bem.Kernel(N, delta, h, E1, nu, np.inf, 0.3) as k:
+        out = ramp.run(k, f, depths, dg, tol=1e-9)
+    assert all(r["status"] == 0 for r in out)
+    Fmin = min(r["force"] for r in out)
+    assert Fmin / F_crit == pytest.approx(1.0, abs=0.12)
+
+
+def test_ramp_resume_repeats_trajectory(cuda, tmp_path):
+    N, R, E, nu = 64, 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Es = E / (1 - nu * nu)
+    dg = (5 * delta) ** 3 * 8 * Es / (np.pi * R * R)
+    f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda)
+    depths = ramp.depth_schedule(0.012, -0.005, 5, 25)
+    ck = str(tmp_path / "ramp.npz")
+    with bem.Kernel(N, delta, np.inf, E, nu, E, nu) as k:
+        full = ramp.run(k, f, depths, dg, tol=1e-11, checkpoint=ck, every=10)
+        state = ramp.load_state(ck)
+        assert state[0] == 30
+        part = ramp.run(k, f, depths[:20], dg, tol=1e-11, checkpoint=ck, every=10)
+        resumed = ramp.run(k, f, depths, dg, tol=1e-11, state=ramp.load_state(ck))
+    assert [r["n_contact"] for r in part + resumed] == [r["n_contact"] for r in full]
+    for a, b in zip(part + resumed, full):
+        assert a["force"] == b["force"]
