@@ -58,6 +58,7 @@ struct SolveState {
   double sum_p;      // sum of pressures after the update
   double scale;      // pending load-control rescale of p (1 = none)
   double uscale;     // rms displacement over the contact set (noise thresholds)
+  double res_replaced; // residual at the last replacement of the recursive gap by the true one
   double pscale;     // mean pressure over the contact set
   double target;     // F under force control
   double delta2;     // delta^2
@@ -78,7 +79,7 @@ struct SolveState {
   int matvecs;
   int mv_p_on;       // gate of the refresh product u = K p (1 = run)
   int mv_t_on;       // gate of the search-direction product (1 = run, i.e. not done)
-  int pad_;
+  int replace;       // 1: recompute the gap from u = K p before the next iteration
 };
 
 // Workspace owned by a kernel handle.

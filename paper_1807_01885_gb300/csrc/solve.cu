@@ -12,6 +12,8 @@
 // residual free of the cancellation in u + f - d; whenever a cell enters or leaves
 // the set, u = K p is recomputed before the next step.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <unordered_set>
@@ -105,7 +107,7 @@ __global__ void k_init_scale(const T* __restrict__ f, const T* __restrict__ q, c
 }
 
 template <typename T>
-__global__ void k_init_apply(const T* __restrict__ f, const T* __restrict__ q, const T* __restrict__ u,
+__global__ void k_init_apply(const T* __restrict__ f, T* __restrict__ q, const T* __restrict__ u,
                              T* __restrict__ p, T* __restrict__ g, const SolveState* st, size_t n) {
   const T s = (T)st->scale;
   const double d = st->d;
@@ -113,21 +115,25 @@ __global__ void k_init_apply(const T* __restrict__ f, const T* __restrict__ q, c
   GRID_STRIDE(i, n) {
     p[i] = s * q[i];
     g[i] = s * u[i] + (f[i] - dT);
+    q[i] = (T)0;   // q's slot holds the pending pressure changes from here on
   }
 }
 
-// Correction of the gap after the contact set changed: the update moved p by
-// -tau t plus a sparse change dp (cells projected to 0 or re-activated), stored in x;
-// with u = K dp the gap becomes g + u, which keeps g a recursively updated residual.
-// Then the pending load rescale: g = s (g + u) + (s - 1)(d - f), p *= s.
+// Correction of the gap after the contact set changed: the updates moved p by -tau t
+// plus a sparse change dp (cells projected to 0 or re-activated since the last
+// correction), accumulated in x; with u = K dp the gap becomes g + u, which keeps g a
+// recursively updated residual; x is cleared.  Then the pending load rescale:
+// g = s (g + u) + (s - 1)(d - f), p *= s.
 template <typename T>
 __global__ void k_gap(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ p, T* __restrict__ g,
-                      const SolveState* st, size_t n) {
+                      T* __restrict__ dp, const SolveState* st, size_t n) {
   if (st->done || !st->refresh) return;
-  const T s = (T)st->scale, s1 = (T)(st->scale - 1.0);
+  const T s = (T)st->scale, s1 = s - (T)1;   // the scale actually applied to p
   const double d = st->d;
   const T dT = (T)d;
+  const T zero[4] = {(T)0, (T)0, (T)0, (T)0};
   VEC_LOOP(i4, n) {
+    st4(dp, i4, zero);
     T uv[4], fv[4], pv[4], gv[4];
     ld4(u, i4, uv);
     ld4(f, i4, fv);
@@ -160,16 +166,35 @@ __global__ void k_init_gap(const T* __restrict__ f, const T* __restrict__ p, T* 
   }
 }
 
+// Replacement of the recursive gap (scheduled by k_pk_begin): dp = p and g = f - d,
+// so that the next correction computes g = K p + f - d from scratch.
+template <typename T>
+__global__ void k_replace(const T* __restrict__ f, const T* __restrict__ p, T* __restrict__ g, T* __restrict__ dp,
+                          const SolveState* st, size_t n) {
+  if (st->done || !st->replace) return;
+  const T dT = (T)st->d;
+  VEC_LOOP(i4, n) {
+    T fv[4], pv[4], gv[4];
+    ld4(f, i4, fv);
+    ld4(p, i4, pv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gv[e] = fv[e] - dT;
+    st4(g, i4, gv);
+    st4(dp, i4, pv);
+  }
+}
+
 // Start of an iteration: apply a pending load rescale (if no refresh did), then
 // sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2.
 template <typename T>
-__global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, double* partials,
-                           unsigned int* ticket, SolveState* st, size_t n) {
+__global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, T* __restrict__ dp,
+                           double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   const double s = st->scale, d = st->d;
   const T dT = (T)d;
   const bool apply = (!st->refresh) && (s != 1.0);
-  const T sT = (T)s, s1 = (T)(s - 1.0);
+  // the gap moves with the scale actually applied to p (the float value of s)
+  const T sT = (T)s, s1 = sT - (T)1;
   Acc<T> ag, agg, auu, ap, cnt;
   VEC_LOOP(i4, n) {
     T pv[4], gv[4], fv[4];
@@ -177,13 +202,17 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
     ld4(g, i4, gv);
     ld4(f, i4, fv);
     if (apply) {
+      T xv[4];
+      ld4(dp, i4, xv);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         pv[e] = sT * pv[e];
         gv[e] = sT * gv[e] + s1 * (dT - fv[e]);
+        xv[e] = sT * xv[e];     // pending changes scale with p
       }
       st4(p, i4, pv);
       st4(g, i4, gv);
+      st4(dp, i4, xv);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -220,9 +249,18 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
       finish(st, BEM_ENAN);
       return;
     }
+    st->replace = 0;
     if (st->res <= st->tol && st->n_neg == 0 && st->n_ol == 0) {
       finish(st, BEM_OK);
       return;
+    }
+    // Reliable updating: whenever the recursive residual has dropped 100-fold since
+    // the gap was last recomputed, recompute it from u = K p (after this step), so the
+    // recursion's drift stays at the rounding level of the residual at that point.
+    // Not near the tolerance: the recomputed gap carries the product's rounding floor.
+    if (st->res <= 1e-2 * st->res_replaced && st->res > 30.0 * st->tol) {
+      st->replace = 1;
+      st->res_replaced = st->res;
     }
     if (st->iter >= st->max_iter) {
       finish(st, BEM_ENOCONV);
@@ -312,20 +350,21 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
     ld4(g, i4, gv);
     ld4(t, i4, tv);
     ld4(r, i4, rv);
+    ld4(dp, i4, dv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const T pi = pv[e], gi = gv[e];
-      T pn, dpn = (T)0;
+      T pn, dpn = dv[e];      // changes not yet applied to g accumulate until the next correction
       if (pi > (T)0) {
         pn = pi - tau * tv[e];
         if (pn < (T)0) {
           if (pn < pthr) nneg.add((T)1);
-          dpn = -pn;          // the projection moves p from pn to 0
+          dpn -= pn;          // the projection moves p from pn to 0
           pn = (T)0;
         }
       } else if (gi < gthr) {
         pn = -tau * gi;
-        dpn = pn;             // re-activation: p moves from 0 to pn
+        dpn += pn;            // re-activation: p moves from 0 to pn
         nol.add((T)1);
       } else {
         pn = (T)0;
@@ -346,8 +385,9 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
     st->n_neg = (int)tot[1];
     st->n_ol = (int)tot[2];
     st->flag = (st->n_ol > 0) ? 0.0 : 1.0;
-    st->refresh = (st->n_neg + st->n_ol > 0) ? 1 : 0;
+    st->refresh = (st->n_neg + st->n_ol > 0 || st->replace) ? 1 : 0;
     st->mv_p_on = st->refresh;
+    if (st->replace) st->flag = 0.0;   // the recomputed gap restarts the conjugate directions
     st->iter += 1;
     st->matvecs += 1 + (st->refresh ? 1 : 0);
     if (st->control == BEM_CTRL_FORCE) {
@@ -653,6 +693,7 @@ bem_status pk_setup(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cu
   init.control = prob->control;
   init.max_iter = prob->max_iter;
   init.n_neg = 1;  // no convergence test passes before one full iteration
+  init.res_replaced = 1e300;
   init.status = BEM_OK;
   init.mv_t_on = 1;
   // products outside the iteration: one for the depth-control initial guess, or the
@@ -700,13 +741,14 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
   unsigned int* tk = k->ws.ticket;
   for (int it = 0; it < CHUNK; ++it) {
     launch_matvec<T>(k, v.x, v.u, s, &st->mv_p_on);
-    k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, st, c.n);
-    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, part, tk, st, c.n);
+    k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, v.x, st, c.n);
+    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, part, tk, st, c.n);
     k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
     launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
     k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
     k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, part, tk, st, c.n);
-    note_launches(5);
+    k_replace<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.p, v.g, v.x, st, c.n);
+    note_launches(6);
   }
 }
 
@@ -748,12 +790,17 @@ template <typename T>
 bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cudaStream_t s) {
   bem_status e = pk_setup<T>(k, prob, pinit, s);
   if (e != BEM_OK) return e;
+  static const bool trace = getenv("BEM_TRACE") != nullptr;   // diagnostic: residual per chunk on stderr
   for (;;) {
     e = pk_chunk<T>(k, s);
     if (e != BEM_OK) return e;
     e = read_state<T>(k, s);
     if (e != BEM_OK) return e;
-    if (k->ws.state_host->done) break;
+    const SolveState* hs = k->ws.state_host;
+    if (trace)
+      fprintf(stderr, "bem: iter %d res %.3e n_c %d neg %d ol %d refresh %d replaced_at %.3e\n", hs->iter, hs->res,
+              hs->n_c, hs->n_neg, hs->n_ol, hs->refresh, hs->res_replaced);
+    if (hs->done) break;
   }
   return BEM_OK;
 }
