@@ -243,8 +243,6 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
     k->col_radix_alt = (alt != nullptr && alt[0] == '1') ? 1 : 0;
     const char* ralt = getenv("BEM_ROW_RADIX_ALT");
     k->row_radix_alt = (ralt != nullptr && ralt[0] == '1') ? 1 : 0;
-    const char* cp = getenv("BEM_COL_PERSIST");
-    k->col_persist = (cp != nullptr && cp[0] == '1') ? 1 : 0;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t n = (size_t)k->N * k->N;

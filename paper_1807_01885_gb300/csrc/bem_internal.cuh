@@ -37,10 +37,14 @@ template <typename C> __device__ __forceinline__ C cmul_pi(C a) { return mk(-a.y
 
 // ---------------------------------------------------------------------------
 // Layout constants.
-// Spectrum (after the row pass) is stored column-block-major: for column block
-// cb (TC consecutive frequencies), an N x TC row-major sub-array:
-//     spec[((cb * N) + r) * TC + tc],  j = cb * TC + tc,  cb in [0, N/TC].
-// The last block holds only the Nyquist column j = N at tc = 0.
+// Spectrum (after the row pass), N >= 16: column-major, spec[j * N + r] for the
+// frequencies j in [0, N] (each column contiguous for the column pass; the row
+// passes move whole 32-byte groups of neighbouring rows through shared memory).
+// N < 16 (the small-grid shared-memory kernels): column-block-major, for column
+// block cb (TC consecutive frequencies) an N x TC row-major sub-array
+//     spec[((cb * N) + r) * TC + tc],  j = cb * TC + tc,  cb in [0, N/TC],
+// the last block holding only the Nyquist column j = N at tc = 0.  Both fit in
+// (N/TC + 1) N TC complex values.
 constexpr int TC = 4;
 constexpr int NTHREADS = 256;
 constexpr int MAX_LOGN = 11;   // N <= 2048
@@ -112,7 +116,6 @@ struct bem_kernel_s {
   int dev;
   int col_radix_alt;   // 1: alternative radix for the column pass (set from BEM_COL_RADIX_ALT)
   int row_radix_alt;   // 1: alternative radix for the row passes (set from BEM_ROW_RADIX_ALT)
-  int col_persist;     // 1: persistent, prefetching column pass (BEM_COL_PERSIST=1)
   bem::Workspace ws;
   // per-pass CUDA-event timing (bem_set_pass_timing): pending (start, end) pairs,
   // harvested into totals at synchronisation points

@@ -10,9 +10,14 @@
 // for the small last stage, thread t holds x[t + T q], q < R, before the first
 // stage and X[t + T q] after the last one (natural order in both).
 //
-// Twiddles come from per-stage tables in global memory laid out [(r-1)/2][j mod Ns][2]
-// (one 16-byte load gives a thread two consecutive twiddles; consecutive threads
-// read consecutive entries), built once per operator.
+// Twiddles w_r = e^{-2 pi i k r/(Ns Q)} (k = j mod Ns) come from per-stage tables in
+// global memory, built once per operator, laid out in planes [plane][k][2] (one
+// 16-byte load per plane in float; consecutive threads read consecutive k).  Float
+// stores a few per k: Q = 16: (w1, w2), (w3, w4), (w8, w12); Q = 8: (w1, w2), (w3, w4);
+// Q = 4: (w1, w2), (w3, -); Q = 2: (w1, -); the others are products of two stored ones
+// (w5 = w1 w4, w9 = w1 w8, w13 = w1 w12, ...), one rounding above a stored value, so
+// that a stage costs 3 loads instead of 8.  Double (where the FP64 pipe, not the loads,
+// bounds the pass) stores all of them: plane p holds (w_{2p+1}, w_{2p+2}).
 #pragma once
 
 #include "bem_internal.cuh"
@@ -139,6 +144,17 @@ __device__ __forceinline__ void dftq(C* v) {
 }
 
 // --- stage plan ----------------------------------------------------------------
+// planes of stored twiddles per k for a stage of radix q (see the header comment)
+template <typename T>
+__host__ __device__ constexpr int tw_planes(int q) {
+  return sizeof(T) == 4 ? (q == 16 ? 3 : (q >= 4 ? 2 : 1)) : q / 2;
+}
+// exponent r of the twiddle held at (plane, e) of a stage of radix q
+template <typename T>
+__host__ __device__ constexpr int tw_exponent(int plane, int e) {
+  return sizeof(T) == 4 ? (plane == 0 ? 1 + e : (plane == 1 ? 3 + e : 8 + 4 * e)) : 2 * plane + 1 + e;
+}
+
 template <int LOGL, int LOGR>
 struct Plan {
   static constexpr int L = 1 << LOGL;
@@ -150,12 +166,13 @@ struct Plan {
   static constexpr int NSTAGES = SR + (LOGRL ? 1 : 0);
   static constexpr int PADL = L + (L >> LOGR);        // padded shared-memory length
   __host__ __device__ static constexpr int radix(int s) { return s < SR ? R : RL; }
-  // twiddle-table offset of stage s (stage 0 has none): stage i >= 1 stores its
-  // radix(i) - 1 twiddles per k in pairs, [pair][k][2], i.e. radix(i) Ns entries
+  // twiddle-table offset of stage s (stage 0 has none): stage i >= 1 stores
+  // tw_planes(radix(i)) planes of Ns pairs
+  template <typename T>
   __host__ __device__ static constexpr int tw_offset(int s) {
     int off = 0, ns = 1;
     for (int i = 0; i < s; ++i) {
-      if (i > 0) off += radix(i) * ns;
+      if (i > 0) off += 2 * tw_planes<T>(radix(i)) * ns;
       ns *= radix(i);
     }
     return off;
@@ -186,6 +203,92 @@ __device__ __forceinline__ const P* opaque(const P* p) {
   return q;
 }
 
+template <bool INV, typename C>
+__device__ __forceinline__ C twmul(C a, C w) { return INV ? cmulc(a, w) : cmul(a, w); }
+
+// (cos, sin)(pi q / 16), q < 16: the constant factors e^{-+ i pi q / R} (R = 16 or 8,
+// index q 16 / R) that relate the twiddles of the points t + (N/R) q to that of t.
+static __constant__ double c_pi16d[16][2] = {
+    {1.0, 0.0},
+    {0.98078528040323044912618223613424, 0.19509032201612826784828486847702},
+    {0.92387953251128675612818318939679, 0.38268343236508977172845998403040},
+    {0.83146961230254523707878837761791, 0.55557023301960222474283081394853},
+    {0.70710678118654752440084436210485, 0.70710678118654752440084436210485},
+    {0.55557023301960222474283081394853, 0.83146961230254523707878837761791},
+    {0.38268343236508977172845998403040, 0.92387953251128675612818318939679},
+    {0.19509032201612826784828486847702, 0.98078528040323044912618223613424},
+    {0.0, 1.0},
+    {-0.19509032201612826784828486847702, 0.98078528040323044912618223613424},
+    {-0.38268343236508977172845998403040, 0.92387953251128675612818318939679},
+    {-0.55557023301960222474283081394853, 0.83146961230254523707878837761791},
+    {-0.70710678118654752440084436210485, 0.70710678118654752440084436210485},
+    {-0.83146961230254523707878837761791, 0.55557023301960222474283081394853},
+    {-0.92387953251128675612818318939679, 0.38268343236508977172845998403040},
+    {-0.98078528040323044912618223613424, 0.19509032201612826784828486847702}};
+static __constant__ float c_pi16f[16][2] = {
+    {1.0f, 0.0f},
+    {0.98078528040323044912618223613424f, 0.19509032201612826784828486847702f},
+    {0.92387953251128675612818318939679f, 0.38268343236508977172845998403040f},
+    {0.83146961230254523707878837761791f, 0.55557023301960222474283081394853f},
+    {0.70710678118654752440084436210485f, 0.70710678118654752440084436210485f},
+    {0.55557023301960222474283081394853f, 0.83146961230254523707878837761791f},
+    {0.38268343236508977172845998403040f, 0.92387953251128675612818318939679f},
+    {0.19509032201612826784828486847702f, 0.98078528040323044912618223613424f},
+    {0.0f, 1.0f},
+    {-0.19509032201612826784828486847702f, 0.98078528040323044912618223613424f},
+    {-0.38268343236508977172845998403040f, 0.92387953251128675612818318939679f},
+    {-0.55557023301960222474283081394853f, 0.83146961230254523707878837761791f},
+    {-0.70710678118654752440084436210485f, 0.70710678118654752440084436210485f},
+    {-0.83146961230254523707878837761791f, 0.55557023301960222474283081394853f},
+    {-0.92387953251128675612818318939679f, 0.38268343236508977172845998403040f},
+    {-0.98078528040323044912618223613424f, 0.19509032201612826784828486847702f}};
+template <typename T> __device__ __forceinline__ cplx<T> pi16(int q);
+template <> __device__ __forceinline__ float2 pi16<float>(int q) { return make_float2(c_pi16f[q][0], c_pi16f[q][1]); }
+template <> __device__ __forceinline__ double2 pi16<double>(int q) { return make_double2(c_pi16d[q][0], c_pi16d[q][1]); }
+
+// Multiplies x(r), r = 1..Q-1, by w_r (conjugated for INV) for one k of a stage whose
+// table planes start at tws (Ns pairs per plane).
+template <int Q, bool INV, typename C, typename X>
+__device__ __forceinline__ void apply_twiddles(const C* tws, int ns, int k, X&& x) {
+  if constexpr (sizeof(C) == 16) {   // double: every twiddle stored
+#pragma unroll
+    for (int pl = 0; pl < Q / 2; ++pl) {
+      C w1, w2;
+      load_pair(tws + 2 * (pl * ns + k), w1, w2);
+      x(2 * pl + 1) = twmul<INV>(x(2 * pl + 1), w1);
+      if (2 * pl + 2 < Q) x(2 * pl + 2) = twmul<INV>(x(2 * pl + 2), w2);
+    }
+    return;
+  }
+  C w1, w2;
+  load_pair(tws + 2 * k, w1, w2);
+  x(1) = twmul<INV>(x(1), w1);
+  if constexpr (Q >= 4) {
+    C w3, w4;
+    load_pair(tws + 2 * (ns + k), w3, w4);
+    x(2) = twmul<INV>(x(2), w2);
+    x(3) = twmul<INV>(x(3), w3);
+    if constexpr (Q >= 8) {
+      x(4) = twmul<INV>(x(4), w4);
+      x(5) = twmul<INV>(x(5), cmul(w1, w4));
+      x(6) = twmul<INV>(x(6), cmul(w2, w4));
+      x(7) = twmul<INV>(x(7), cmul(w3, w4));
+    }
+    if constexpr (Q == 16) {
+      C w8, w12;
+      load_pair(tws + 2 * (2 * ns + k), w8, w12);
+      x(8) = twmul<INV>(x(8), w8);
+      x(9) = twmul<INV>(x(9), cmul(w1, w8));
+      x(10) = twmul<INV>(x(10), cmul(w2, w8));
+      x(11) = twmul<INV>(x(11), cmul(w3, w8));
+      x(12) = twmul<INV>(x(12), w12);
+      x(13) = twmul<INV>(x(13), cmul(w1, w12));
+      x(14) = twmul<INV>(x(14), cmul(w2, w12));
+      x(15) = twmul<INV>(x(15), cmul(w3, w12));
+    }
+  }
+}
+
 // Full transform on the thread's registers v[q] = x[t + T q] -> X[t + T q].
 // sh: this transform's padded shared buffer (PADL complex).  HALF: x = 0 for
 // index >= L/2 (v[R/2..R-1] zero on entry).  All threads of the block must call it
@@ -200,34 +303,14 @@ __device__ __forceinline__ void reg_fft(cplx<T>* v, cplx<T>* sh, const cplx<T>* 
   for (int s = 0; s < P::NSTAGES; ++s) {
     const bool small = (s == P::SR);   // the radix-RL stage
     if (s > 0) {
-      const C* tws = opaque(tw + P::tw_offset(s));
+      const C* tws = opaque(tw + P::template tw_offset<T>(s));
       if (!small) {
-        const int k = t & (ns - 1);
-#pragma unroll
-        for (int pr = 0; pr < R / 2; ++pr) {
-          C w1, w2;
-          load_pair(tws + 2 * (pr * ns + k), w1, w2);
-          const int r1 = 2 * pr + 1, r2 = 2 * pr + 2;
-          v[r1] = INV ? cmulc(v[r1], w1) : cmul(v[r1], w1);
-          if (r2 < R) v[r2] = INV ? cmulc(v[r2], w2) : cmul(v[r2], w2);
-        }
+        apply_twiddles<R, INV>(tws, ns, t & (ns - 1), [&](int r) -> C& { return v[r]; });
       } else {
 #pragma unroll
         for (int b = 0; b < R / RL; ++b) {
-          const int j = t + TT * b;
-          const int k = j & (ns - 1);
-#pragma unroll
-          for (int pr = 0; pr < RL / 2; ++pr) {
-            C w1, w2;
-            load_pair(tws + 2 * (pr * ns + k), w1, w2);
-            const int r1 = 2 * pr + 1, r2 = 2 * pr + 2;
-            C& x1 = v[b + r1 * (R / RL)];
-            x1 = INV ? cmulc(x1, w1) : cmul(x1, w1);
-            if (r2 < RL) {
-              C& x2 = v[b + r2 * (R / RL)];
-              x2 = INV ? cmulc(x2, w2) : cmul(x2, w2);
-            }
-          }
+          const int k = (t + TT * b) & (ns - 1);
+          apply_twiddles<RL, INV>(tws, ns, k, [&](int r) -> C& { return v[b + r * (R / RL)]; });
         }
       }
     }
