@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=48, help="instances of the batch workload (0: skip)")
     ap.add_argument("--warmstart", type=int, default=512,
                     help="training solutions for the learned warm start (0: skip)")
+    ap.add_argument("--probe-matvec", type=int, default=0, metavar="K",
+                    help="only run K operator products at N=2048 (FP32) and exit: the small case "
+                         "that the ncu summaries under profiles/ capture")
     return ap.parse_args()
 
 
@@ -130,8 +133,10 @@ class Clocks:
 
 
 PROFILE = os.path.join(ROOT, "profiles", "col_pass_N2048_fp32.md")
+# the sources of the three FFT passes (the column pass, its FFT and its launch);
+# a change to any of them invalidates the captured traffic
 PROFILED_SOURCES = ["paper_1807_01885_gb300/csrc/matvec_reg.cuh", "paper_1807_01885_gb300/csrc/fft_reg.cuh",
-                    "paper_1807_01885_gb300/csrc/bem_internal.cuh", "paper_1807_01885_gb300/csrc/matvec_f32.cu"]
+                    "paper_1807_01885_gb300/csrc/matvec_f32.cu"]
 
 
 def profiled_traffic():
@@ -465,8 +470,29 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def probe_matvec(count):
+    """K products u = K p of one N = 2048 FP32 operator (h/delta = 16, E1/E2 = 2,
+    nu = 0.3) on four random pressure fields; prints nothing but 'ok'."""
+    import torch
+    from paper_1807_01885_gb300 import bem, build
+    build.build()
+    N = N_GRID
+    k = bem.Kernel(N, 1.0 / N, 16.0 / N, 2.0, 0.3, 1.0, 0.3, precision="fp32")
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    P = [torch.rand((N, N), dtype=torch.float32, device="cuda", generator=gen) for _ in range(4)]
+    U = [torch.empty_like(x) for x in P]
+    for it in range(count):
+        k.matvec(P[it % 4], U[it % 4])
+    torch.cuda.synchronize()
+    k.close()
+    print("ok")
+
+
 def main():
     args = parse()
+    if args.probe_matvec > 0:
+        probe_matvec(args.probe_matvec)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

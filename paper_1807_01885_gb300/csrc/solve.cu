@@ -119,36 +119,6 @@ __global__ void k_init_apply(const T* __restrict__ f, T* __restrict__ q, const T
   }
 }
 
-// Correction of the gap after the contact set changed: the updates moved p by -tau t
-// plus a sparse change dp (cells projected to 0 or re-activated since the last
-// correction), accumulated in x; with u = K dp the gap becomes g + u, which keeps g a
-// recursively updated residual; x is cleared.  Then the pending load rescale:
-// g = s (g + u) + (s - 1)(d - f), p *= s.
-template <typename T>
-__global__ void k_gap(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ p, T* __restrict__ g,
-                      T* __restrict__ dp, const SolveState* st, size_t n) {
-  if (st->done || !st->refresh) return;
-  const T s = (T)st->scale, s1 = s - (T)1;   // the scale actually applied to p
-  const double d = st->d;
-  const T dT = (T)d;
-  const T zero[4] = {(T)0, (T)0, (T)0, (T)0};
-  VEC_LOOP(i4, n) {
-    st4(dp, i4, zero);
-    T uv[4], fv[4], pv[4], gv[4];
-    ld4(u, i4, uv);
-    ld4(f, i4, fv);
-    ld4(p, i4, pv);
-    ld4(g, i4, gv);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      gv[e] = s * (gv[e] + uv[e]) + s1 * (dT - fv[e]);
-      pv[e] = s * pv[e];
-    }
-    st4(g, i4, gv);
-    st4(p, i4, pv);
-  }
-}
-
 // Start values for a warm or uniform start: g = f - d (the gap of p = 0) and dp = p,
 // so that the first correction gives g = K p + f - d.
 template <typename T>
@@ -166,42 +136,45 @@ __global__ void k_init_gap(const T* __restrict__ f, const T* __restrict__ p, T* 
   }
 }
 
-// Replacement of the recursive gap (scheduled by k_pk_begin): dp = p and g = f - d,
-// so that the next correction computes g = K p + f - d from scratch.
-template <typename T>
-__global__ void k_replace(const T* __restrict__ f, const T* __restrict__ p, T* __restrict__ g, T* __restrict__ dp,
-                          const SolveState* st, size_t n) {
-  if (st->done || !st->replace) return;
-  const T dT = (T)st->d;
-  VEC_LOOP(i4, n) {
-    T fv[4], pv[4], gv[4];
-    ld4(f, i4, fv);
-    ld4(p, i4, pv);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) gv[e] = fv[e] - dT;
-    st4(g, i4, gv);
-    st4(dp, i4, pv);
-  }
-}
-
-// Start of an iteration: apply a pending load rescale (if no refresh did), then
-// sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2.
+// Start of an iteration.
+// After a change of the contact set (refresh): the updates moved p by -tau t plus a
+// sparse change dp (cells projected to 0 or re-activated since the last correction),
+// accumulated in x; with u = K dp the gap becomes g + u, which keeps g a recursively
+// updated residual; x is cleared.  (When a replacement was scheduled, x holds the
+// whole of p and g = f - d, so this recomputes g = K p + f - d from scratch.)
+// Without a refresh only a pending load rescale is applied, with x scaled along.
+// Either way with the scale s actually applied to p: g = s g' + (s - 1)(d - f), p *= s.
+// Then sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2, sum p.
 template <typename T>
 __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, T* __restrict__ dp,
-                           double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+                           const T* __restrict__ u, double* partials, unsigned int* ticket, SolveState* st,
+                           size_t n) {
   if (st->done) return;
   const double s = st->scale, d = st->d;
   const T dT = (T)d;
-  const bool apply = (!st->refresh) && (s != 1.0);
+  const bool refresh = st->refresh != 0;
+  const bool apply = (!refresh) && (s != 1.0);
   // the gap moves with the scale actually applied to p (the float value of s)
   const T sT = (T)s, s1 = sT - (T)1;
+  const T zero[4] = {(T)0, (T)0, (T)0, (T)0};
   Acc<T> ag, agg, auu, ap, cnt;
   VEC_LOOP(i4, n) {
     T pv[4], gv[4], fv[4];
     ld4(p, i4, pv);
     ld4(g, i4, gv);
     ld4(f, i4, fv);
-    if (apply) {
+    if (refresh) {
+      T uv[4];
+      ld4(u, i4, uv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        gv[e] = sT * (gv[e] + uv[e]) + s1 * (dT - fv[e]);
+        pv[e] = sT * pv[e];
+      }
+      st4(p, i4, pv);
+      st4(g, i4, gv);
+      st4(dp, i4, zero);
+    } else if (apply) {
       T xv[4];
       ld4(dp, i4, xv);
 #pragma unroll
@@ -332,12 +305,17 @@ __global__ void k_pk_rt(const T* __restrict__ p, const T* __restrict__ g, const 
 }
 
 // Update: p -= tau t on Ic with projection to p >= 0; cells outside Ic with a
-// negative gap re-enter with p = -tau g; g -= tau K t.
+// negative gap re-enter with p = -tau g; g -= tau K t.  When k_pk_begin scheduled a
+// replacement of the recursive gap, the step instead leaves x = p and g = f - d, so
+// that the next correction computes g = K p + f - d from scratch.
 template <typename T>
 __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
-                            T* __restrict__ dp, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+                            T* __restrict__ dp, const T* __restrict__ f, double* partials, unsigned int* ticket,
+                            SolveState* st, size_t n) {
   if (st->done) return;
   const T tau = (T)st->tau;
+  const bool replace = st->replace != 0;
+  const T dT = (T)st->d;
   // Rounding-noise thresholds (float path only): a re-activation needs a gap below
   // -noise * rms(u) and a projection counts as a change of the contact set only when
   // the pressure went below -noise * mean(p).  In double both thresholds are 0.
@@ -373,6 +351,15 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
       dv[e] = dpn;
       gv[e] = gi - tau * rv[e];
       asum.add(pn);
+    }
+    if (replace) {
+      T fv[4];
+      ld4(f, i4, fv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        dv[e] = pv[e];
+        gv[e] = fv[e] - dT;
+      }
     }
     st4(p, i4, pv);
     st4(g, i4, gv);
@@ -741,14 +728,12 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
   unsigned int* tk = k->ws.ticket;
   for (int it = 0; it < CHUNK; ++it) {
     launch_matvec<T>(k, v.x, v.u, s, &st->mv_p_on);
-    k_gap<T><<<c.eb, NTHREADS, 0, s>>>(v.u, v.f, v.p, v.g, v.x, st, c.n);
-    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, part, tk, st, c.n);
+    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, v.u, part, tk, st, c.n);
     k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
     launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
     k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
-    k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, part, tk, st, c.n);
-    k_replace<T><<<c.eb, NTHREADS, 0, s>>>(v.f, v.p, v.g, v.x, st, c.n);
-    note_launches(6);
+    k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, v.f, part, tk, st, c.n);
+    note_launches(4);
   }
 }
 
