@@ -144,15 +144,18 @@ __device__ __forceinline__ void dftq(C* v) {
 }
 
 // --- stage plan ----------------------------------------------------------------
+// float stages store a few twiddles and form the rest as products
+template <typename T>
+__host__ __device__ constexpr bool tw_products() { return sizeof(T) == 4; }
 // planes of stored twiddles per k for a stage of radix q (see the header comment)
 template <typename T>
 __host__ __device__ constexpr int tw_planes(int q) {
-  return sizeof(T) == 4 ? (q == 16 ? 3 : (q >= 4 ? 2 : 1)) : q / 2;
+  return tw_products<T>() ? (q == 16 ? 3 : (q >= 4 ? 2 : 1)) : q / 2;
 }
 // exponent r of the twiddle held at (plane, e) of a stage of radix q
 template <typename T>
 __host__ __device__ constexpr int tw_exponent(int plane, int e) {
-  return sizeof(T) == 4 ? (plane == 0 ? 1 + e : (plane == 1 ? 3 + e : 8 + 4 * e)) : 2 * plane + 1 + e;
+  return tw_products<T>() ? (plane == 0 ? 1 + e : (plane == 1 ? 3 + e : 8 + 4 * e)) : 2 * plane + 1 + e;
 }
 
 template <int LOGL, int LOGR>
@@ -250,7 +253,7 @@ template <> __device__ __forceinline__ double2 pi16<double>(int q) { return make
 // table planes start at tws (Ns pairs per plane).
 template <int Q, bool INV, typename C, typename X>
 __device__ __forceinline__ void apply_twiddles(const C* tws, int ns, int k, X&& x) {
-  if constexpr (sizeof(C) == 16) {   // double: every twiddle stored
+  if constexpr (!tw_products<decltype(C::x)>()) {   // every twiddle stored
 #pragma unroll
     for (int pl = 0; pl < Q / 2; ++pl) {
       C w1, w2;
@@ -289,12 +292,32 @@ __device__ __forceinline__ void apply_twiddles(const C* tws, int ns, int k, X&& 
   }
 }
 
+// Synchronisation of the threads of one transform around its exchanges.  When a
+// block holds several transforms, each exchanges through its own buffer, so it
+// waits only for its own threads: one warp (__syncwarp), or a named barrier per
+// transform (ids 1..15, id 0 being __syncthreads); otherwise the whole block.
+template <int TT, int PER_BLOCK>
+struct GroupSync {
+  static constexpr int kind = (PER_BLOCK == 1) ? 0 : (TT == 32 ? 1 : ((TT > 32 && PER_BLOCK <= 15) ? 2 : 0));
+  __device__ __forceinline__ static void sync(int group) {
+    if constexpr (kind == 1) {
+      __syncwarp();
+    } else if constexpr (kind == 2) {
+      asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(TT) : "memory");
+    } else {
+      __syncthreads();
+    }
+  }
+};
+
 // Full transform on the thread's registers v[q] = x[t + T q] -> X[t + T q].
 // sh: this transform's padded shared buffer (PADL complex).  HALF: x = 0 for
-// index >= L/2 (v[R/2..R-1] zero on entry).  All threads of the block must call it
-// (it contains __syncthreads).
-template <int LOGL, int LOGR, bool INV, bool HALF, typename T>
-__device__ __forceinline__ void reg_fft(cplx<T>* v, cplx<T>* sh, const cplx<T>* __restrict__ tw, int t) {
+// index >= L/2 (v[R/2..R-1] zero on entry).  PER_BLOCK transforms share the block;
+// group is this one's index (see GroupSync).  All threads of the group (of the block
+// when the block-wide barrier is used) must call it.
+template <int LOGL, int LOGR, bool INV, bool HALF, typename T, int PER_BLOCK = 1>
+__device__ __forceinline__ void reg_fft(cplx<T>* v, cplx<T>* sh, const cplx<T>* __restrict__ tw, int t,
+                                        int group = 0) {
   using C = cplx<T>;
   using P = Plan<LOGL, LOGR>;
   constexpr int R = P::R, TT = P::T, RL = P::RL;
@@ -334,10 +357,10 @@ __device__ __forceinline__ void reg_fft(cplx<T>* v, cplx<T>* sh, const cplx<T>* 
       const int base = (t / ns) * ns * R + (t & (ns - 1));
 #pragma unroll
       for (int r = 0; r < R; ++r) sh[padi<LOGR>(base + r * ns)] = v[r];
-      __syncthreads();
+      GroupSync<TT, PER_BLOCK>::sync(group);
 #pragma unroll
       for (int q = 0; q < R; ++q) v[q] = sh[padi<LOGR>(t + TT * q)];
-      __syncthreads();
+      GroupSync<TT, PER_BLOCK>::sync(group);
     }
     ns *= small ? RL : R;
   }

@@ -67,7 +67,7 @@ k_row_fwd_r(const T* __restrict__ p, cplx<T>* __restrict__ spec, const cplx<T>* 
   for (int q = 0; q < R / 2; ++q) v[q] = prow[t + TT * q];
 #pragma unroll
   for (int q = R / 2; q < R; ++q) v[q] = mk((T)0, (T)0);
-  reg_fft<LOGN, LOGR, false, true, T>(v, sh, twr, t);
+  reg_fft<LOGN, LOGR, false, true, T, RPB>(v, sh, twr, t, rl);
 #pragma unroll
   for (int q = 0; q < R; ++q) sh[padi<LOGR>(t + TT * q)] = v[q];
   __syncthreads();
@@ -131,7 +131,7 @@ k_row_inv_r(const cplx<T>* __restrict__ spec, T* __restrict__ u, const cplx<T>* 
     v[q] = cadd(e, o);
   }
   __syncthreads();
-  reg_fft<LOGN, LOGR, true, false, T>(v, sh, twr, t);
+  reg_fft<LOGN, LOGR, true, false, T, RPB>(v, sh, twr, t, rl);
   C* urow = reinterpret_cast<C*>(u + (size_t)(r0 + rl) * N);
 #pragma unroll
   for (int q = 0; q < R / 2; ++q) urow[t + TT * q] = v[q];
@@ -157,7 +157,7 @@ k_col_r(cplx<T>* __restrict__ spec, const T* __restrict__ table, const cplx<T>* 
   for (int q = 0; q < R / 2; ++q) v[q] = active ? col[t + TT * q] : mk((T)0, (T)0);
 #pragma unroll
   for (int q = R / 2; q < R; ++q) v[q] = mk((T)0, (T)0);
-  reg_fft<LOGM, LOGR, false, true, T>(v, sh, twc, t);
+  reg_fft<LOGM, LOGR, false, true, T, CPB>(v, sh, twc, t, c);
   const T* kt = table + (size_t)slot * (N + 4);   // column j = slot of the square table (row stride N + 4)
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -166,7 +166,7 @@ k_col_r(cplx<T>* __restrict__ spec, const T* __restrict__ table, const cplx<T>* 
     const T kv = active ? kt[f] : (T)0;
     v[q] = cscale(v[q], kv);
   }
-  reg_fft<LOGM, LOGR, true, false, T>(v, sh, twc, t);
+  reg_fft<LOGM, LOGR, true, false, T, CPB>(v, sh, twc, t, c);
   if (active) {
 #pragma unroll
     for (int q = 0; q < R / 2; ++q) col[t + TT * q] = v[q];
