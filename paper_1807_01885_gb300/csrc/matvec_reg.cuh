@@ -35,6 +35,14 @@ __device__ __forceinline__ cplx<T> recomb_tw(const cplx<T>* __restrict__ tw, cpl
   else return tw[j];
 }
 
+// asynchronous global -> shared copy of one complex value (8 or 16 bytes, L1-cached)
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* smem, const C* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(a), "l"(gmem), "n"(sizeof(C)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // rows per block of the row passes and columns per block of the column pass
 template <typename T, int LOGN, int LOGR>
 __host__ __device__ constexpr int rows_per_block() {
@@ -108,16 +116,18 @@ k_row_inv_r(const cplx<T>* __restrict__ spec, T* __restrict__ u, const cplx<T>* 
   const int rl = threadIdx.x / TT, t = threadIdx.x - rl * TT;
   const int r0 = blockIdx.x * RPB;
   C* sh = sh0 + rl * SH;
-  // column-major load of the RPB rows' half spectra Y[j], j in [0, N]
+  // column-major load of the RPB rows' half spectra Y[j], j in [0, N], copied
+  // asynchronously from global to shared memory (no register staging)
   const C* in = spec + r0;
 #pragma unroll
   for (int k = 0; k < (RPB * (N + 1) + NT - 1) / NT; ++k) {
     const int e = threadIdx.x + NT * k;
     if (e < RPB * (N + 1)) {
       const int j = e / RPB, rr = e - j * RPB;
-      sh0[rr * SH + j] = in[(size_t)j * N + rr];
+      cp_async_elem(sh0 + rr * SH + j, in + (size_t)j * N + rr);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   C v[R];
   const C wt = sizeof(T) == 4 ? tw[t] : mk((T)0, (T)0);
