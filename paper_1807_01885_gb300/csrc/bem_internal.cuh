@@ -84,6 +84,7 @@ struct SolveState {
   int mv_p_on;       // gate of the refresh product u = K p (1 = run)
   int mv_t_on;       // gate of the search-direction product (1 = run, i.e. not done)
   int replace;       // 1: recompute the gap from u = K p before the next iteration
+  int x_clear;       // 1: this iteration consumed x (its correction ran), so the update rewrites x from 0
 };
 
 // Workspace owned by a kernel handle.
@@ -95,7 +96,7 @@ struct Workspace {
   void* twr = nullptr;       // stage twiddles of the length-N register FFT (rows)
   void* twc = nullptr;       // stage twiddles of the length-2N register FFT (columns)
   void* vec = nullptr;       // solver vectors: p, g, t, r, u, f, x (N*N each)
-  uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy
+  uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy; PK: contact set {p > 0}
   double* partials = nullptr;// per-block partial sums
   unsigned int* ticket = nullptr;
   SolveState* state = nullptr;

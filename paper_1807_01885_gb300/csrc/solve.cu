@@ -83,6 +83,21 @@ __device__ __forceinline__ void finish(SolveState* st, int status) {
 
 // Initial guess for depth control: q = max(d - f, 0) scaled by the energy-optimal
 // factor s = <q, d - f> / <q, K q>; the gap then follows from u = K q as s u + f - d.
+// contact-set bytes of four consecutive cells: (p > 0) written by k_pk_begin, read
+// by the sweeps that need only the set (p keeps its sign until k_pk_update)
+template <typename T>
+__device__ __forceinline__ void stm4(uint8_t* m, size_t i4, const T (&pv)[4]) {
+  reinterpret_cast<uchar4*>(m)[i4] =
+      make_uchar4(pv[0] > (T)0, pv[1] > (T)0, pv[2] > (T)0, pv[3] > (T)0);
+}
+__device__ __forceinline__ void ldm4(const uint8_t* m, size_t i4, bool (&o)[4]) {
+  const uchar4 v = reinterpret_cast<const uchar4*>(m)[i4];
+  o[0] = v.x != 0;
+  o[1] = v.y != 0;
+  o[2] = v.z != 0;
+  o[3] = v.w != 0;
+}
+
 template <typename T>
 __global__ void k_init_q(const T* __restrict__ f, T* __restrict__ q, double d, size_t n) {
   const T dT = (T)d;
@@ -140,15 +155,16 @@ __global__ void k_init_gap(const T* __restrict__ f, const T* __restrict__ p, T* 
 // After a change of the contact set (refresh): the updates moved p by -tau t plus a
 // sparse change dp (cells projected to 0 or re-activated since the last correction),
 // accumulated in x; with u = K dp the gap becomes g + u, which keeps g a recursively
-// updated residual; x is cleared.  (When a replacement was scheduled, x holds the
+// updated residual; x counts as cleared (k_pk_update rewrites it from 0).  (When a replacement was scheduled, x holds the
 // whole of p and g = f - d, so this recomputes g = K p + f - d from scratch.)
 // Without a refresh only a pending load rescale is applied, with x scaled along.
 // Either way with the scale s actually applied to p: g = s g' + (s - 1)(d - f), p *= s.
-// Then sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2, sum p.
+// Then sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2, sum p,
+// and the set itself as bytes for the sweeps up to the update.
 template <typename T>
 __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, T* __restrict__ dp,
-                           const T* __restrict__ u, double* partials, unsigned int* ticket, SolveState* st,
-                           size_t n) {
+                           const T* __restrict__ u, uint8_t* __restrict__ cm, double* partials,
+                           unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   const double s = st->scale, d = st->d;
   const T dT = (T)d;
@@ -156,7 +172,6 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
   const bool apply = (!refresh) && (s != 1.0);
   // the gap moves with the scale actually applied to p (the float value of s)
   const T sT = (T)s, s1 = sT - (T)1;
-  const T zero[4] = {(T)0, (T)0, (T)0, (T)0};
   Acc<T> ag, agg, auu, ap, cnt;
   VEC_LOOP(i4, n) {
     T pv[4], gv[4], fv[4];
@@ -173,7 +188,6 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
       }
       st4(p, i4, pv);
       st4(g, i4, gv);
-      st4(dp, i4, zero);
     } else if (apply) {
       T xv[4];
       ld4(dp, i4, xv);
@@ -187,6 +201,7 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
       st4(g, i4, gv);
       st4(dp, i4, xv);
     }
+    stm4(cm, i4, pv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (pv[e] > (T)0) {
@@ -203,6 +218,7 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
   double tot[5];
   if (grid_reduce<5>(v, partials, ticket, tot)) {
     st->scale = 1.0;
+    st->x_clear = refresh ? 1 : 0;   // x was consumed by this iteration's correction
     st->refresh = 0;
     st->n_c = (int)tot[1];
     if (st->n_c == 0) {
@@ -247,20 +263,21 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
 
 // Search direction: g -= gbar (force control), t = g + beta t on Ic, 0 elsewhere.
 template <typename T>
-__global__ void k_pk_dir(const T* __restrict__ p, T* __restrict__ g, T* __restrict__ t, const SolveState* st,
+__global__ void k_pk_dir(const uint8_t* __restrict__ cm, T* __restrict__ g, T* __restrict__ t, const SolveState* st,
                          size_t n) {
   if (st->done) return;
   const T gbar = (T)st->gbar, beta = (T)st->beta;
   const bool shift = st->gbar != 0.0;
   VEC_LOOP(i4, n) {
-    T pv[4], gv[4], tv[4];
-    ld4(p, i4, pv);
+    T gv[4], tv[4];
+    bool in[4];
+    ldm4(cm, i4, in);
     ld4(g, i4, gv);
     ld4(t, i4, tv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (shift) gv[e] -= gbar;
-      tv[e] = (pv[e] > (T)0) ? gv[e] + beta * tv[e] : (T)0;
+      tv[e] = in[e] ? gv[e] + beta * tv[e] : (T)0;
     }
     if (shift) st4(g, i4, gv);
     st4(t, i4, tv);
@@ -269,19 +286,20 @@ __global__ void k_pk_dir(const T* __restrict__ p, T* __restrict__ g, T* __restri
 
 // Step length: tau = <g, t>_Ic / <r - rbar, t>_Ic with r = K t.
 template <typename T>
-__global__ void k_pk_rt(const T* __restrict__ p, const T* __restrict__ g, const T* __restrict__ t,
+__global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g, const T* __restrict__ t,
                         const T* __restrict__ r, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   Acc<T> art, ar, at, agt;
   VEC_LOOP(i4, n) {
-    T pv[4], gv[4], tv[4], rv[4];
-    ld4(p, i4, pv);
+    T gv[4], tv[4], rv[4];
+    bool in[4];
+    ldm4(cm, i4, in);
     ld4(g, i4, gv);
     ld4(t, i4, tv);
     ld4(r, i4, rv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (pv[e] > (T)0) {
+      if (in[e]) {
         art.add(rv[e] * tv[e]);
         ar.add(rv[e]);
         at.add(tv[e]);
@@ -315,6 +333,7 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
   if (st->done) return;
   const T tau = (T)st->tau;
   const bool replace = st->replace != 0;
+  const bool xz = st->x_clear != 0;   // x consumed this iteration: accumulate from 0
   const T dT = (T)st->d;
   // Rounding-noise thresholds (float path only): a re-activation needs a gap below
   // -noise * rms(u) and a projection counts as a change of the contact set only when
@@ -323,12 +342,12 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
   const T gthr = -noise * (T)st->uscale, pthr = -noise * (T)st->pscale;
   Acc<T> asum, nneg, nol;
   VEC_LOOP(i4, n) {
-    T pv[4], gv[4], tv[4], rv[4], dv[4];
+    T pv[4], gv[4], tv[4], rv[4], dv[4] = {(T)0, (T)0, (T)0, (T)0};
     ld4(p, i4, pv);
     ld4(g, i4, gv);
     ld4(t, i4, tv);
     ld4(r, i4, rv);
-    ld4(dp, i4, dv);
+    if (!xz) ld4(dp, i4, dv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const T pi = pv[e], gi = gv[e];
@@ -726,12 +745,13 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
   SolveState* st = k->ws.state;
   double* part = k->ws.partials;
   unsigned int* tk = k->ws.ticket;
+  uint8_t* cm = k->ws.mask;   // contact set of the iterations (the adhesive masks are not live here)
   for (int it = 0; it < CHUNK; ++it) {
     launch_matvec<T>(k, v.x, v.u, s, &st->mv_p_on);
-    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, v.u, part, tk, st, c.n);
-    k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.p, v.g, v.t, st, c.n);
+    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, v.u, cm, part, tk, st, c.n);
+    k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(cm, v.g, v.t, st, c.n);
     launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
-    k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, part, tk, st, c.n);
+    k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(cm, v.g, v.t, v.r, part, tk, st, c.n);
     k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, v.f, part, tk, st, c.n);
     note_launches(4);
   }
