@@ -261,13 +261,14 @@ __global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __rest
   }
 }
 
-// Search direction: g -= gbar (force control), t = g + beta t on Ic, 0 elsewhere.
+// Search direction: t = (g - gbar) + beta t on Ic, 0 elsewhere (gbar: force control).
+// The shifted gap g - gbar is not stored: k_pk_rt and k_pk_update form the same
+// float value from g when they read it, and k_pk_update stores the shifted step.
 template <typename T>
-__global__ void k_pk_dir(const uint8_t* __restrict__ cm, T* __restrict__ g, T* __restrict__ t, const SolveState* st,
-                         size_t n) {
+__global__ void k_pk_dir(const uint8_t* __restrict__ cm, const T* __restrict__ g, T* __restrict__ t,
+                         const SolveState* st, size_t n) {
   if (st->done) return;
   const T gbar = (T)st->gbar, beta = (T)st->beta;
-  const bool shift = st->gbar != 0.0;
   VEC_LOOP(i4, n) {
     T gv[4], tv[4];
     bool in[4];
@@ -275,20 +276,17 @@ __global__ void k_pk_dir(const uint8_t* __restrict__ cm, T* __restrict__ g, T* _
     ld4(g, i4, gv);
     ld4(t, i4, tv);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      if (shift) gv[e] -= gbar;
-      tv[e] = in[e] ? gv[e] + beta * tv[e] : (T)0;
-    }
-    if (shift) st4(g, i4, gv);
+    for (int e = 0; e < 4; ++e) tv[e] = in[e] ? (gv[e] - gbar) + beta * tv[e] : (T)0;
     st4(t, i4, tv);
   }
 }
 
-// Step length: tau = <g, t>_Ic / <r - rbar, t>_Ic with r = K t.
+// Step length: tau = <g - gbar, t>_Ic / <r - rbar, t>_Ic with r = K t.
 template <typename T>
 __global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g, const T* __restrict__ t,
                         const T* __restrict__ r, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
+  const T gbar = (T)st->gbar;
   Acc<T> art, ar, at, agt;
   VEC_LOOP(i4, n) {
     T gv[4], tv[4], rv[4];
@@ -303,7 +301,7 @@ __global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g,
         art.add(rv[e] * tv[e]);
         ar.add(rv[e]);
         at.add(tv[e]);
-        agt.add(gv[e] * tv[e]);
+        agt.add((gv[e] - gbar) * tv[e]);
       }
     }
   }
@@ -323,7 +321,7 @@ __global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g,
 }
 
 // Update: p -= tau t on Ic with projection to p >= 0; cells outside Ic with a
-// negative gap re-enter with p = -tau g; g -= tau K t.  When k_pk_begin scheduled a
+// negative gap re-enter with p = -tau g; g -= tau K t (g here the shifted gap g - gbar).  When k_pk_begin scheduled a
 // replacement of the recursive gap, the step instead leaves x = p and g = f - d, so
 // that the next correction computes g = K p + f - d from scratch.
 template <typename T>
@@ -335,6 +333,7 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
   const bool replace = st->replace != 0;
   const bool xz = st->x_clear != 0;   // x consumed this iteration: accumulate from 0
   const T dT = (T)st->d;
+  const T gbar = (T)st->gbar;          // the shift of k_pk_dir, applied here to the stored gap
   // Rounding-noise thresholds (float path only): a re-activation needs a gap below
   // -noise * rms(u) and a projection counts as a change of the contact set only when
   // the pressure went below -noise * mean(p).  In double both thresholds are 0.
@@ -350,7 +349,7 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
     if (!xz) ld4(dp, i4, dv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const T pi = pv[e], gi = gv[e];
+      const T pi = pv[e], gi = gv[e] - gbar;
       T pn, dpn = dv[e];      // changes not yet applied to g accumulate until the next correction
       if (pi > (T)0) {
         pn = pi - tau * tv[e];
