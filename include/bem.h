@@ -146,6 +146,26 @@ bem_status bem_solve_batch(int32_t n, const bem_kernel* kernels, const bem_probl
 bem_status bem_profile_passes(bem_kernel k, const void* p, void* u, int32_t reps, float* ms_out,
                               void* cuda_stream);
 
+/* FFT radix of the register passes (N >= 16; an implementation choice, no
+ * counterpart in the paper).  Each row and column transform runs as stages of
+ * radix 2^row_log2_radix / 2^col_log2_radix (3: radix 8, 4: radix 16) with one
+ * shared-memory exchange between stages; results agree to rounding either way.
+ * bem_set_radix rebuilds the stage twiddle tables on cuda_stream and drops the
+ * handle's captured CG-iteration graph (the next solve on a capturable stream
+ * captures it again).  The float path accepts 3 or 4 for each; the double path only
+ * 3.  Other values give BEM_EINVAL; N < 16 ignores the call.  Synchronises the
+ * stream. */
+bem_status bem_set_radix(bem_kernel k, int32_t row_log2_radix, int32_t col_log2_radix, void* cuda_stream);
+
+/* Autotuner of those choices: times every allowed radix of the row passes (forward
+ * and inverse together) and of the column pass, `reps` launches each (CUDA events on
+ * cuda_stream, minimum over the launches), on the handle's own workspace, keeps the
+ * fastest of each and writes it to choice_out[0] (rows) and choice_out[1] (columns),
+ * as log2 of the radix (choice_out may be NULL).  Costs about 4 reps products;
+ * leaves the handle as bem_set_radix with the chosen values does.  Synchronises the
+ * stream. */
+bem_status bem_autotune(bem_kernel k, int32_t reps, int32_t* choice_out, void* cuda_stream);
+
 /* u = K p for callers that cannot allocate device memory (no counterpart in the
  * paper; an integration aid).  Some callers may not call cudaMalloc at all: code
  * running under a host framework's memory pool that must not be bypassed, real-time

@@ -29,7 +29,8 @@ EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_mat
            "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_set_pass_timing", "bem_pass_timing",
            "bem_launch_count", "bem_last_error", "bem_version", "bem_fno_create", "bem_fno_destroy",
            "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features", "bem_fno_forward",
-           "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure")
+           "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure", "bem_set_radix",
+           "bem_autotune")
 BEM_STATIC_MAX_N = 256
 
 
@@ -115,6 +116,10 @@ def load(path=None):
                  "bem_fno_forward", "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure"):
         getattr(lib, name).restype = i32
     lib.bem_set_pass_timing.argtypes = [vp, i32]
+    lib.bem_set_radix.argtypes = [vp, i32, i32, vp]
+    lib.bem_set_radix.restype = i32
+    lib.bem_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), vp]
+    lib.bem_autotune.restype = i32
     lib.bem_set_pass_timing.restype = i32
     lib.bem_pass_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
     lib.bem_pass_timing.restype = i32
@@ -225,6 +230,18 @@ def bem_matvec_static(N, delta, h, E1, nu1, E2, nu2, p, u, dc_mode=BEM_DC_FINITE
     return u
 
 
+def bem_set_radix(k, row_log2_radix, col_log2_radix, stream=None):
+    _check(load().bem_set_radix(k, row_log2_radix, col_log2_radix, _stream(stream)))
+
+
+def bem_autotune(k, reps=10, stream=None):
+    """Times the allowed FFT radices of the row and column passes and keeps the
+    fastest; returns (rows, columns) as log2 of the radix."""
+    c = (ctypes.c_int32 * 2)()
+    _check(load().bem_autotune(k, reps, c, _stream(stream)))
+    return int(c[0]), int(c[1])
+
+
 def bem_set_pass_timing(k, on):
     _check(load().bem_set_pass_timing(k, 1 if on else 0))
 
@@ -281,6 +298,13 @@ class Kernel:
         prob = make_problem(height, ctrl, target, dgamma, tol, max_iter, p_init, contact_mask)
         res = bem_solve_contact(self.handle, prob, p_out, stream)
         return p_out, res
+
+    def set_radix(self, rows, cols, stream=None):
+        """log2 of the FFT radix of the row and column passes (3 or 4; 3 only in fp64)."""
+        bem_set_radix(self.handle, rows, cols, stream)
+
+    def autotune(self, reps=10, stream=None):
+        return bem_autotune(self.handle, reps, stream)
 
     def close(self):
         if getattr(self, "handle", None):

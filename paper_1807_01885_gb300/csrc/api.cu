@@ -224,6 +224,108 @@ bem_status bem_pass_timing(bem_kernel k, double* ms_total, int64_t* launches_out
   return BEM_OK;
 }
 
+// ---- radix choice and autotuner ---------------------------------------------
+static int cur_row_log2(const bem_kernel_s* k) { return (k->prec == BEM_FP32 && !k->row_radix_alt) ? 4 : 3; }
+static int cur_col_log2(const bem_kernel_s* k) { return (k->prec == BEM_FP32 && !k->col_radix_alt) ? 4 : 3; }
+
+// Sets the radix flags, rebuilds the stage twiddles and drops the captured CG graph
+// (it holds launches of the previous kernels).  Asynchronous on s.
+static bem_status apply_radix(bem_kernel_s* k, int row_log2, int col_log2, cudaStream_t s) {
+  const bool f32 = k->prec == BEM_FP32;
+  k->row_radix_alt = (f32 && row_log2 == 3) ? 1 : 0;
+  k->col_radix_alt = (f32 && col_log2 == 3) ? 1 : 0;
+  if (f32) reg_twiddles<float>(k, s);
+  else reg_twiddles<double>(k, s);
+  note_launches(2);
+  BEM_CUDA_TRY(cudaGetLastError());
+  if (k->graphs.pk_exec != nullptr) {
+    BEM_CUDA_TRY(cudaGraphExecDestroy(k->graphs.pk_exec));
+    k->graphs.pk_exec = nullptr;
+    k->graphs.pk_nodes = 0;
+  }
+  k->graphs.warm = 0;   // the next chunk runs plainly once (attributes of the new kernels)
+  return BEM_OK;
+}
+
+static bool radix_allowed(const bem_kernel_s* k, int v) { return v == 3 || (k->prec == BEM_FP32 && v == 4); }
+
+bem_status bem_set_radix(bem_kernel k, int32_t row_log2_radix, int32_t col_log2_radix, void* cuda_stream) {
+  if (k == nullptr) { set_error("NULL kernel"); return BEM_EINVAL; }
+  if (!radix_allowed(k, row_log2_radix) || !radix_allowed(k, col_log2_radix)) {
+    set_error("log2 radix must be 3 (or 4 on the float path)");
+    return BEM_EINVAL;
+  }
+  if (k->logN < 4) return BEM_OK;
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  bem_status st = apply_radix(k, row_log2_radix, col_log2_radix, s);
+  if (st != BEM_OK) return st;
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_autotune(bem_kernel k, int32_t reps, int32_t* choice_out, void* cuda_stream) {
+  if (k == nullptr || reps <= 0) { set_error("invalid autotune arguments"); return BEM_EINVAL; }
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int best_row = cur_row_log2(k), best_col = cur_col_log2(k);
+  if (k->logN >= 4 && k->prec == BEM_FP32) {
+    // input and output of the timed passes: two of the handle's solver vectors
+    const size_t n = (size_t)k->N * k->N;
+    float* pin = (float*)k->ws.vec + 6 * n;
+    float* uout = (float*)k->ws.vec + 4 * n;
+    BEM_CUDA_TRY(cudaMemsetAsync(pin, 0x3f, n * sizeof(float), s));   // finite values (0.747...)
+    cudaEvent_t e0, e1;
+    BEM_CUDA_TRY(cudaEventCreate(&e0));
+    BEM_CUDA_TRY(cudaEventCreate(&e1));
+    // minimum time over reps of the row passes (0 and 2) or the column pass (1),
+    // after two untimed launches
+    auto time_passes = [&](bool rows) -> float {
+      float best = 1e30f;
+      for (int r = 0; r < reps + 2; ++r) {
+        cudaEventRecord(e0, s);
+        if (rows) {
+          launch_pass<float>(k, 0, pin, uout, s);
+          launch_pass<float>(k, 2, pin, uout, s);
+        } else {
+          launch_pass<float>(k, 1, pin, uout, s);
+        }
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r >= 2 && ms < best) best = ms;
+      }
+      return best;
+    };
+    bem_status st = BEM_OK;
+    float t_best = 1e30f;
+    for (int cand : {4, 3}) {   // rows: forward and inverse passes together
+      if ((st = apply_radix(k, cand, best_col, s)) != BEM_OK) break;
+      const float t = time_passes(true);
+      if (t < t_best) { t_best = t; best_row = cand; }
+    }
+    t_best = 1e30f;
+    for (int cand : {4, 3}) {   // columns
+      if (st != BEM_OK) break;
+      if ((st = apply_radix(k, best_row, cand, s)) != BEM_OK) break;
+      const float t = time_passes(false);
+      if (t < t_best) { t_best = t; best_col = cand; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != BEM_OK) return st;
+    BEM_CUDA_TRY(cudaGetLastError());
+    if ((st = apply_radix(k, best_row, best_col, s)) != BEM_OK) return st;
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  if (choice_out != nullptr) {
+    choice_out[0] = best_row;
+    choice_out[1] = best_col;
+  }
+  return BEM_OK;
+}
+
 bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out) {
   if (out == nullptr) { set_error("out is NULL"); return BEM_EINVAL; }
   *out = nullptr;

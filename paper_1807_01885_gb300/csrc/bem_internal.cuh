@@ -90,7 +90,7 @@ struct SolveState {
 // Workspace owned by a kernel handle.
 struct Workspace {
   void* spec = nullptr;      // (N/TC + 1) * N * TC complex
-  void* table = nullptr;     // (N/TC + 1) * (N+1) * TC real, blocked, scaled by 1/M^2
+  void* table = nullptr;     // K^/M^2 in the path precision: N >= 16 (N+1) rows of N+4 (row j = column j), else blocked
   double* table64 = nullptr; // (N+1)^2 doubles, unscaled, row-major
   void* tw = nullptr;        // M complex: e^{-2 pi i k / M}
   void* twr = nullptr;       // stage twiddles of the length-N register FFT (rows)
@@ -115,8 +115,8 @@ struct bem_kernel_s {
   int prec;       // BEM_FP64 / BEM_FP32
   size_t elem;    // sizeof(real)
   int dev;
-  int col_radix_alt;   // 1: alternative radix for the column pass (set from BEM_COL_RADIX_ALT)
-  int row_radix_alt;   // 1: alternative radix for the row passes (set from BEM_ROW_RADIX_ALT)
+  int col_radix_alt;   // 1: radix 8 for the float column pass (bem_set_radix, bem_autotune, BEM_COL_RADIX_ALT)
+  int row_radix_alt;   // 1: radix 8 for the float row passes (bem_set_radix, bem_autotune, BEM_ROW_RADIX_ALT)
   bem::Workspace ws;
   // per-pass CUDA-event timing (bem_set_pass_timing): pending (start, end) pairs,
   // harvested into totals at synchronisation points
