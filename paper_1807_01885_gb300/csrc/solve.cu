@@ -43,10 +43,10 @@ DV<T> dv(const bem_kernel_s* k) {
 // Share of the contact set whose re-entry in one step restarts the conjugate
 // directions.  Polonsky and Keer restart on any re-entry; on rough surfaces, where a
 // few cells re-enter in most steps, that turns the iteration into steepest descent
-// (at N = 1024, 193 of 218 steps restarted).  Keeping the recurrence through small
+// (at N = 1024, 193 of 218 steps restarted).  Keeping the recurrence through smaller
 // re-entries reaches the same solution (the stopping test is unchanged) in 2-3 times
 // fewer steps; a direction that is not a descent direction still restarts.
-constexpr double kRestartShare = 0.01;
+constexpr double kRestartShare = 0.1;   // 1 %: 27.5 ms, 10 %: 26.0 ms at N = 2048 (GB300)
 
 int red_blocks(size_t n) {
   // two blocks per SM: the last block then adds few partials
