@@ -48,10 +48,11 @@ DV<T> dv(const bem_kernel_s* k) {
 // fewer steps; a direction that is not a descent direction still restarts.
 constexpr double kRestartShare = 0.1;   // 1 %: 27.5 ms, 10 %: 26.0 ms at N = 2048 (GB300)
 
-int red_blocks(size_t n) {
-  // two blocks per SM: the last block then adds few partials
+// Blocks of a reduction sweep: per_sm blocks per SM (one wave at the kernel's register
+// count; more resident threads keep more loads in flight), fewer for small n.
+int red_blocks(size_t n, int per_sm) {
   size_t b = (n + NTHREADS * 16 - 1) / (NTHREADS * 16);
-  if (b > 2 * 152) b = 2 * 152;
+  if (b > (size_t)per_sm * 152) b = (size_t)per_sm * 152;
   b = std::max<size_t>(1, std::min<size_t>(b, RED_MAX_BLOCKS));
   return (int)b;
 }
@@ -170,7 +171,7 @@ __global__ void k_init_gap(const T* __restrict__ f, const T* __restrict__ p, T* 
 // Then sums over the contact set Ic = {p > 0}: sum g, count, sum g^2, sum u^2, sum p,
 // and the set itself as bytes for the sweeps up to the update.
 template <typename T>
-__global__ void k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, T* __restrict__ dp,
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, T* __restrict__ dp,
                            const T* __restrict__ u, uint8_t* __restrict__ cm, double* partials,
                            unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
@@ -291,7 +292,7 @@ __global__ void k_pk_dir(const uint8_t* __restrict__ cm, const T* __restrict__ g
 
 // Step length: tau = <g - gbar, t>_Ic / <r - rbar, t>_Ic with r = K t.
 template <typename T>
-__global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g, const T* __restrict__ t,
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 1) k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g, const T* __restrict__ t,
                         const T* __restrict__ r, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
   if (st->done) return;
   const T gbar = (T)st->gbar;
@@ -339,7 +340,7 @@ __global__ void k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g,
 // replacement of the recursive gap, the step instead leaves x = p and g = f - d, so
 // that the next correction computes g = K p + f - d from scratch.
 template <typename T>
-__global__ void k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
                             T* __restrict__ dp, const T* __restrict__ f, double* partials, unsigned int* ticket,
                             SolveState* st, size_t n) {
   if (st->done) return;
@@ -648,14 +649,15 @@ bem_status read_state(bem_kernel_s* k, cudaStream_t s) {
 
 struct Ctx {
   size_t n;
-  int rb, eb;
+  int rb, rb6, eb;   // reduction blocks (4 and 6 per SM), element-wise blocks
 };
 
 template <typename T>
 Ctx ctx_of(const bem_kernel_s* k) {
   Ctx c;
   c.n = (size_t)k->N * k->N;
-  c.rb = red_blocks(c.n);
+  c.rb = red_blocks(c.n, 4);
+  c.rb6 = red_blocks(c.n, 6);
   c.eb = (int)std::min<size_t>((c.n / 4 + NTHREADS - 1) / NTHREADS, 152 * 8);
   return c;
 }
@@ -768,7 +770,7 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
     k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, v.u, cm, part, tk, st, c.n);
     k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(cm, v.g, v.t, st, c.n);
     launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
-    k_pk_rt<T><<<c.rb, NTHREADS, 0, s>>>(cm, v.g, v.t, v.r, part, tk, st, c.n);
+    k_pk_rt<T><<<sizeof(T) == 4 ? c.rb6 : c.rb, NTHREADS, 0, s>>>(cm, v.g, v.t, v.r, part, tk, st, c.n);
     k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, v.f, part, tk, st, c.n);
     note_launches(4);
   }
