@@ -20,6 +20,7 @@ template <typename T> struct Acc;
 template <> struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add4(const double (&x)[4]) { s += (x[0] + x[1]) + (x[2] + x[3]); }
   __device__ __forceinline__ void combine(const Acc& o) { s += o.s; }
   __device__ __forceinline__ Acc shfl_down(int o) const {
     Acc r;
@@ -41,6 +42,9 @@ template <> struct Acc<float> {
     lo += (hi - (t - bp)) + (x - bp);
     hi = t;
   }
+  // four terms of one 16-byte group: summed pairwise in float (each term carries its
+  // own float rounding already), then one compensated addition
+  __device__ __forceinline__ void add4(const float (&x)[4]) { add((x[0] + x[1]) + (x[2] + x[3])); }
   __device__ __forceinline__ void combine(const Acc& o) {
     const float t = hi + o.hi;
     const float bp = t - hi;
@@ -96,11 +100,20 @@ __device__ bool grid_reduce(Acc<T> (&a)[NS], double* __restrict__ partials, unsi
   if (!last) return false;
   __threadfence();
   __syncthreads();
+  // every partial this thread adds is loaded in one unrolled pass (all loads in
+  // flight at once); each sum still combines its partials in block order
+  Acc<T> xs[NS];
+#pragma unroll
+  for (int k = 0; k < RED_MAX_BLOCKS / NTHREADS; ++k) {
+    const int b = threadIdx.x + k * NTHREADS;
+    if (b < (int)gridDim.x) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) xs[s].combine(Acc<T>::from(__ldcg(&partials[s * RED_MAX_BLOCKS + b])));
+    }
+  }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    Acc<T> x;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += NTHREADS)
-      x.combine(Acc<T>::from(__ldcg(&partials[s * RED_MAX_BLOCKS + b])));
+    Acc<T> x = xs[s];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x.combine(x.shfl_down(o));
     if (lane == 0) sh[s][warp] = x;

@@ -211,17 +211,22 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T
       st4(dp, i4, xv);
     }
     stm4(cm, i4, pv);
+    T sg[4], sgg[4], suu[4], sp[4], sc[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (pv[e] > (T)0) {
-        const T ui = gv[e] - (fv[e] - dT);
-        ag.add(gv[e]);
-        agg.add(gv[e] * gv[e]);
-        auu.add(ui * ui);
-        ap.add(pv[e]);
-        cnt.add((T)1);
-      }
+      const bool in = pv[e] > (T)0;
+      const T ui = gv[e] - (fv[e] - dT);
+      sg[e] = in ? gv[e] : (T)0;
+      sgg[e] = in ? gv[e] * gv[e] : (T)0;
+      suu[e] = in ? ui * ui : (T)0;
+      sp[e] = in ? pv[e] : (T)0;
+      sc[e] = in ? (T)1 : (T)0;
     }
+    ag.add4(sg);
+    agg.add4(sgg);
+    auu.add4(suu);
+    ap.add4(sp);
+    cnt.add4(sc);
   }
   Acc<T> v[5] = {ag, cnt, agg, auu, ap};
   double tot[5];
@@ -304,15 +309,18 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 1) k_pk_rt(cons
     ld4(g, i4, gv);
     ld4(t, i4, tv);
     ld4(r, i4, rv);
+    T srt[4], sr[4], st_[4], sgt[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (in[e]) {
-        art.add(rv[e] * tv[e]);
-        ar.add(rv[e]);
-        at.add(tv[e]);
-        agt.add((gv[e] - gbar) * tv[e]);
-      }
+      srt[e] = in[e] ? rv[e] * tv[e] : (T)0;
+      sr[e] = in[e] ? rv[e] : (T)0;
+      st_[e] = in[e] ? tv[e] : (T)0;
+      sgt[e] = in[e] ? (gv[e] - gbar) * tv[e] : (T)0;
     }
+    art.add4(srt);
+    ar.add4(sr);
+    at.add4(st_);
+    agt.add4(sgt);
   }
   Acc<T> v[4] = {art, ar, at, agt};
   double tot[4];
@@ -362,29 +370,34 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_update(
     ld4(t, i4, tv);
     ld4(r, i4, rv);
     if (!xz) ld4(dp, i4, dv);
+    T cneg[4], col[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const T pi = pv[e], gi = gv[e] - gbar;
       T pn, dpn = dv[e];      // changes not yet applied to g accumulate until the next correction
+      cneg[e] = (T)0;
+      col[e] = (T)0;
       if (pi > (T)0) {
         pn = pi - tau * tv[e];
         if (pn < (T)0) {
-          if (pn < pthr) nneg.add((T)1);
+          if (pn < pthr) cneg[e] = (T)1;
           dpn -= pn;          // the projection moves p from pn to 0
           pn = (T)0;
         }
       } else if (gi < gthr) {
         pn = -tau * gi;
         dpn += pn;            // re-activation: p moves from 0 to pn
-        nol.add((T)1);
+        col[e] = (T)1;
       } else {
         pn = (T)0;
       }
       pv[e] = pn;
       dv[e] = dpn;
       gv[e] = gi - tau * rv[e];
-      asum.add(pn);
     }
+    asum.add4(pv);
+    nneg.add4(cneg);
+    nol.add4(col);
     if (replace) {
       T fv[4];
       ld4(f, i4, fv);
