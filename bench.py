@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="instances of the batch workload (0: skip)")
     ap.add_argument("--warmstart", type=int, default=512,
                     help="training solutions for the learned warm start (0: skip)")
+    ap.add_argument("--radix", default=None, metavar="ROWS,COLS",
+                    help="log2 FFT radices to use instead of the autotuner's choice (e.g. 4,4); for "
+                         "profiling runs, where the autotuner's timings would be taken under the profiler")
     ap.add_argument("--probe-matvec", type=int, default=0, metavar="K",
                     help="only run K operator products at N=2048 (FP32) and exit: the small case "
                          "that the ncu summaries under profiles/ capture")
@@ -161,11 +164,15 @@ class RadixCache:
     """FFT radix per grid size, picked by the library's autotuner on the first kernel
     of that size and applied to the later ones."""
 
-    def __init__(self):
+    def __init__(self, fixed=None):
         self.choice = {}
+        self.fixed = fixed
 
     def apply(self, k, stream=None):
-        if k.N not in self.choice:
+        if self.fixed is not None:
+            k.set_radix(*self.fixed, stream=stream)
+            self.choice[k.N] = tuple(self.fixed)
+        elif k.N not in self.choice:
             self.choice[k.N] = k.autotune(reps=5, stream=stream)
         else:
             k.set_radix(*self.choice[k.N], stream=stream)
@@ -354,7 +361,7 @@ def run_ours(args):
     # a non-default stream: solves replay their captured CG iteration graphs
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-    radix = RadixCache()
+    radix = RadixCache(tuple(int(x) for x in args.radix.split(",")) if args.radix else None)
     insts = make_instances(torch, dev, bem, inputs, radix)
 
     def step(i):
@@ -465,7 +472,7 @@ def run_ours(args):
             "l2": "working set ~170 MB per solve > 129 MB L2 (no flush needed); matvec-only loop cycles 8 "
                   "distinct 16.8 MB inputs",
             "fft_log2_radix": {"rows": radix.choice[N_GRID][0], "cols": radix.choice[N_GRID][1],
-                               "picked_by": "bem_autotune"},
+                               "picked_by": "--radix" if args.radix else "bem_autotune"},
         },
         "time_to_converge_ms": ms_max / args.steps,
         "cg_iters_per_solve": iters / args.steps,

@@ -1,7 +1,7 @@
 // Grid-wide sums with a deterministic last-block finish.
 //
 // Each thread accumulates its elements; the block combines its threads (warp
-// shuffles, then shared memory) and writes one double per sum to `partials`; the
+// shuffles, then shared memory) and writes one 8-byte partial per sum to `partials`; the
 // last block to arrive (an atomic ticket, no waiting) adds the per-block values in
 // block order and hands the totals to thread 0, which updates the solver scalars.
 // Results are bitwise reproducible for a fixed grid size.
@@ -9,7 +9,7 @@
 // Float data: GB300 runs double-precision arithmetic at a small fraction of the
 // float rate, so the thread and block levels keep each running sum as an
 // unevaluated pair (hi, lo) of floats, combined with Knuth's TwoSum (about 44 bits
-// of mantissa); only the block partials and the final totals are doubles.
+// of mantissa), block partials included; only the final totals are doubles.
 #pragma once
 
 #include "bem_internal.cuh"
@@ -28,9 +28,11 @@ template <> struct Acc<double> {
     return r;
   }
   __device__ __forceinline__ double value() const { return s; }
-  __device__ __forceinline__ static Acc from(double x) {
+  // a block partial in its 8-byte slot
+  __device__ __forceinline__ void store(double* slot) const { *slot = s; }
+  __device__ __forceinline__ static Acc load(const double* slot) {
     Acc r;
-    r.s = x;
+    r.s = __ldcg(slot);
     return r;
   }
 };
@@ -60,10 +62,14 @@ template <> struct Acc<float> {
     return r;
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-  __device__ __forceinline__ static Acc from(double x) {
+  // a block partial in its 8-byte slot, kept as the float pair: the last block then
+  // combines partials without double arithmetic (a small fraction of the float rate)
+  __device__ __forceinline__ void store(double* slot) const { *reinterpret_cast<float2*>(slot) = make_float2(hi, lo); }
+  __device__ __forceinline__ static Acc load(const double* slot) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(slot));
     Acc r;
-    r.hi = (float)x;
-    r.lo = (float)(x - (double)r.hi);
+    r.hi = v.x;
+    r.lo = v.y;
     return r;
   }
 };
@@ -90,7 +96,7 @@ __device__ bool grid_reduce(Acc<T> (&a)[NS], double* __restrict__ partials, unsi
     for (int s = 0; s < NS; ++s) {
       Acc<T> acc = sh[s][0];
       for (int w = 1; w < NTHREADS / 32; ++w) acc.combine(sh[s][w]);
-      partials[s * RED_MAX_BLOCKS + blockIdx.x] = acc.value();
+      acc.store(&partials[s * RED_MAX_BLOCKS + blockIdx.x]);
     }
     __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
@@ -108,7 +114,7 @@ __device__ bool grid_reduce(Acc<T> (&a)[NS], double* __restrict__ partials, unsi
     const int b = threadIdx.x + k * NTHREADS;
     if (b < (int)gridDim.x) {
 #pragma unroll
-      for (int s = 0; s < NS; ++s) xs[s].combine(Acc<T>::from(__ldcg(&partials[s * RED_MAX_BLOCKS + b])));
+      for (int s = 0; s < NS; ++s) xs[s].combine(Acc<T>::load(&partials[s * RED_MAX_BLOCKS + b]));
     }
   }
 #pragma unroll
