@@ -98,14 +98,15 @@ __device__ bool grid_reduce(Acc<T> (&a)[NS], double* __restrict__ partials, unsi
       for (int w = 1; w < NTHREADS / 32; ++w) acc.combine(sh[s][w]);
       acc.store(&partials[s * RED_MAX_BLOCKS + blockIdx.x]);
     }
-    __threadfence();
-    const unsigned int t = atomicAdd(ticket, 1u);
+    // one acquire-release atomic: the release publishes this block's partials, the
+    // acquire (in the block that draws the last ticket) makes every block's visible;
+    // the barrier below extends that to the block's other threads
+    unsigned int t;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(t) : "l"(ticket) : "memory");
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return false;
-  __threadfence();
-  __syncthreads();
   // every partial this thread adds is loaded in one unrolled pass (all loads in
   // flight at once); each sum still combines its partials in block order
   Acc<T> xs[NS];
