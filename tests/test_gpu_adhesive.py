@@ -1,4 +1,6 @@
-"""Adhesive contact on the GPU against the paper's asymptotic solutions (Sec. 3).
+"""Adhesive contact on the GPU against the paper's asymptotic solutions (Sec. 3):
+JKR in the homogeneous limit, the thin-layer flat punch of Fig. 3 (Eq. 16), and the
+sphere of Fig. 5 for all five adhesion parameters (Eqs. 19, 22, 26).
 
 Each case runs the displacement-controlled procedure of Sec. 2 with the detachment
 stress of Eq. (12); the results must approach the closed forms within the
@@ -57,25 +59,56 @@ def test_thin_layer_flat_punch_critical_point(cuda):
     assert out[-1]["n_contact"] == 0
 
 
-def test_thin_layer_sphere_fig5_alpha15(cuda):
-    """Fig. 5, alpha = 15 (a >> h): rigid base, E1 = 1e9, nu1 = 0.3, h = 2 mm,
-    dgamma = 100; the pull-off force approaches F_crit = -2 pi R dgamma (Eqs. 19-21)."""
+# Fig. 5: sphere on a layer over a rigid base for the five adhesion parameters alpha
+# (Eq. 26); E1 = 1e9, nu1 = 0.3, h = 2 mm, dgamma = 100, R from alpha.  The normalised
+# pull-off force F_min / (pi R dgamma) must lie between the JKR limit -3/2 (contact much
+# smaller than the layer) and the thin-layer limit -2 (Eq. 19), decrease with alpha,
+# follow the thick-layer expansion (Eqs. 22/23) where a/h is small (alpha = 0.1, 0.2)
+# and approach Eq. 19 for alpha = 15.  N = 512: the pull-off contact radius spans
+# about 85 cells.
+FIG5_ALPHAS = [0.1, 0.2, 0.5, 2.0, 15.0]
+FIG5_RESULTS = {}
+
+
+def _fig5_ramp(cuda, alpha, N=512):
     E1, nu, h, dg = 1e9, 0.3, 2e-3, 100.0
-    R = 15.0 * np.sqrt(okernel.e_star(E1, nu) * h ** 3 / (2 * dg))
-    d_crit, a_crit, F_crit = analytic.thin_layer_sphere_critical(R, h, E1, nu, dg)
-    N = 512
-    L = 4 * 1.5 * a_crit
-    delta = L / N
-    assert delta < h / 2
+    Es = okernel.e_star(E1, nu)
+    R = alpha * np.sqrt(Es * h ** 3 / (2 * dg))
+    assert analytic.adhesion_parameter(dg, R, E1, nu, h) == pytest.approx(alpha, rel=1e-12)
+    a_F = (9 * np.pi * R * R * dg / (8 * Es)) ** (1 / 3)        # JKR pull-off radius
+    d_c, a_c, F_c = analytic.thin_layer_sphere_critical(R, h, E1, nu, dg)
+    a_ref = min(a_F, a_c)                                        # the relevant limit's radius
+    delta = 6 * a_ref / N
     f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda)
-    a_max = 1.5 * a_crit
-    d_max = analytic.thin_layer_sphere(a_max, R, h, E1, nu, 0.0)[1]
-    depths = ramp.depth_schedule(d_max, 1.3 * d_crit, 8, 80)
+    d_max = (1.5 * a_ref) ** 2 / R
+    d_end = 1.3 * min(analytic.jkr_jump_off(R, Es, dg)[2], d_c)
+    depths = ramp.depth_schedule(d_max, d_end, 8, 70)
     with bem.Kernel(N, delta, h, E1, nu, np.inf, 0.3) as k:
         out = ramp.run(k, f, depths, dg, tol=1e-9)
+    return out, R, h, E1, nu, dg, a_ref
+
+
+@pytest.mark.parametrize("alpha", FIG5_ALPHAS)
+def test_fig5_pull_off_force_between_limits(cuda, alpha):
+    out, R, h, E1, nu, dg, a_ref = _fig5_ramp(cuda, alpha)
     assert all(r["status"] == 0 for r in out)
-    Fmin = min(r["force"] for r in out)
-    assert Fmin / F_crit == pytest.approx(1.0, abs=0.12)
+    assert out[-1]["n_contact"] == 0
+    ratio = min(r["force"] for r in out) / (np.pi * R * dg)
+    FIG5_RESULTS[alpha] = ratio
+    assert -2.0 * 1.01 < ratio < -1.5 * 0.97
+    if alpha <= 0.2:
+        a = np.linspace(0.05, 2.5, 4000) * a_ref
+        thick = np.min(analytic.thick_layer_sphere(a, R, h, E1, nu, dg)[0]) / (np.pi * R * dg)
+        assert ratio / thick == pytest.approx(1.0, abs=0.04)
+    if alpha >= 15:
+        assert ratio / -2.0 == pytest.approx(1.0, abs=0.06)
+
+
+def test_fig5_pull_off_force_decreases_with_alpha(cuda):
+    if len(FIG5_RESULTS) < len(FIG5_ALPHAS):
+        pytest.skip("needs the five runs of test_fig5_pull_off_force_between_limits in this session")
+    vals = [FIG5_RESULTS[a] for a in FIG5_ALPHAS]
+    assert all(b < a for a, b in zip(vals, vals[1:])), vals
 
 
 def test_ramp_resume_repeats_trajectory(cuda, tmp_path):
