@@ -59,6 +59,19 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_ranks(torch, ms, units, device):
+    """Whole-job figures of a timed region run on every rank: the slowest rank's
+    time (max) and the units all ranks processed (sum).  Returns (ms, units); a
+    single process returns its own values."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(ms), float(units)
+    t = torch.tensor([float(ms), float(units)], dtype=torch.float64, device=device)
+    tm, tu = t[0:1].clone(), t[1:2].clone()
+    torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(tu, op=torch.distributed.ReduceOp.SUM)
+    return float(tm[0]), float(tu[0])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -394,13 +407,7 @@ def run_ours(args):
     clk = clocks.stop()
     mv = sum(r["matvecs"] for r in results)
     iters = sum(r["iters"] for r in results)
-    t = torch.tensor([ms, float(mv)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tt = t.clone()
-        torch.distributed.all_reduce(tt[0:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:2], op=torch.distributed.ReduceOp.SUM)
-        t = tt
-    ms_max, mv_all = float(t[0]), float(t[1])
+    ms_max, mv_all = aggregate_ranks(torch, ms, mv, dev)
     value = mv_all / (ms_max / 1000.0)
 
     # second timed region, same steps with the library recording CUDA events around
@@ -458,7 +465,8 @@ def run_ours(args):
         e2e_mv += res["matvecs"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = e2e_mv * world / e2e_s
+    e2e_ms, e2e_all = aggregate_ranks(torch, 1000.0 * e2e_s, e2e_mv, dev)
+    e2e_value = e2e_all / (e2e_ms / 1000.0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
