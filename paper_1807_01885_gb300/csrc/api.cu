@@ -243,7 +243,13 @@ static bem_status apply_radix(bem_kernel_s* k, int row_log2, int col_log2, cudaS
     k->graphs.pk_exec = nullptr;
     k->graphs.pk_nodes = 0;
   }
+  if (k->graphs.lin_exec != nullptr) {
+    BEM_CUDA_TRY(cudaGraphExecDestroy(k->graphs.lin_exec));
+    k->graphs.lin_exec = nullptr;
+    k->graphs.lin_nodes = 0;
+  }
   k->graphs.warm = 0;   // the next chunk runs plainly once (attributes of the new kernels)
+  k->graphs.lin_warm = 0;
   return BEM_OK;
 }
 
@@ -397,6 +403,7 @@ bem_status bem_destroy_kernel(bem_kernel k) {
   cudaDeviceSynchronize();
   harvest_pass_timing(k);
   if (k->graphs.pk_exec != nullptr) cudaGraphExecDestroy(k->graphs.pk_exec);
+  if (k->graphs.lin_exec != nullptr) cudaGraphExecDestroy(k->graphs.lin_exec);
   for (auto& e : k->timing.pool) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);

@@ -128,11 +128,16 @@ struct bem_kernel_s {
     long long n[3] = {0, 0, 0};
   };
   mutable PassTiming timing;
-  // captured CG iteration chunk (replayed by solves on this handle)
+  // captured iteration chunks (replayed by solves on this handle): the constrained
+  // CG of non-adhesive solves and the fixed-area linear CG of adhesive ones
   struct Graphs {
     int warm = 0;                      // one chunk ran plainly (kernel attributes are set)
     cudaGraphExec_t pk_exec = nullptr;
     long long pk_nodes = 0;            // kernel nodes in pk_exec (launch accounting)
+    int lin_warm = 0;
+    cudaGraphExec_t lin_exec = nullptr;
+    long long lin_nodes = 0;
+    const void* lin_mask = nullptr;    // contact mask the linear chunk was captured with
   };
   Graphs graphs;
 };

@@ -789,38 +789,74 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
   }
 }
 
-// One chunk: replay of the handle's captured graph when the stream allows capture
-// and pass timing is off (timing needs events around individual passes); plain
-// launches otherwise.  The first chunk on a handle always runs plainly, so one-time
-// kernel attributes are set outside any capture.
-template <typename T>
-bem_status pk_chunk(bem_kernel_s* k, cudaStream_t s) {
+// One chunk: replay of a captured graph of it when the stream allows capture and
+// pass timing is off (timing needs events around individual passes); plain launches
+// otherwise.  The first chunk of each kind on a handle always runs plainly, so
+// one-time kernel attributes are set outside any capture.
+template <typename F>
+bem_status chunk_graph(const bem_kernel_s* k, cudaStream_t s, cudaGraphExec_t& exec, long long& nodes, int& warm,
+                       F&& chunk_launches) {
   const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
-  if (!capturable || k->timing.on || !k->graphs.warm) {
-    pk_chunk_launches<T>(k, s);
-    k->graphs.warm = 1;
+  if (!capturable || k->timing.on || !warm) {
+    chunk_launches();
+    warm = 1;
     BEM_CUDA_TRY(cudaGetLastError());
     return BEM_OK;
   }
-  if (k->graphs.pk_exec == nullptr) {
+  if (exec == nullptr) {
     cudaGraph_t g = nullptr;
     const long long before = launches();
     BEM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    pk_chunk_launches<T>(k, s);
+    chunk_launches();
     cudaError_t e = cudaStreamEndCapture(s, &g);
-    k->graphs.pk_nodes = launches() - before;
-    note_launches(-k->graphs.pk_nodes);
+    nodes = launches() - before;
+    note_launches(-nodes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&k->graphs.pk_exec, g, 0);
+    e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      k->graphs.pk_exec = nullptr;
+      exec = nullptr;
       return cuda_fail(e, "cudaGraphInstantiate");
     }
   }
-  BEM_CUDA_TRY(cudaGraphLaunch(k->graphs.pk_exec, s));
-  note_launches(k->graphs.pk_nodes);
+  BEM_CUDA_TRY(cudaGraphLaunch(exec, s));
+  note_launches(nodes);
   return BEM_OK;
+}
+
+template <typename T>
+bem_status pk_chunk(bem_kernel_s* k, cudaStream_t s) {
+  auto& gr = k->graphs;
+  return chunk_graph(k, s, gr.pk_exec, gr.pk_nodes, gr.warm, [&] { pk_chunk_launches<T>(k, s); });
+}
+
+// CHUNK iterations of the fixed-area linear CG (adhesive inner solve), gated by the
+// device state like the constrained CG's chunk.
+template <typename T>
+void lin_chunk_launches(bem_kernel_s* k, const uint8_t* C, cudaStream_t s) {
+  const Ctx c = ctx_of<T>(k);
+  DV<T> v = dv<T>(k);
+  SolveState* st = k->ws.state;
+  double* part = k->ws.partials;
+  unsigned int* tk = k->ws.ticket;
+  for (int it = 0; it < CHUNK; ++it) {
+    launch_matvec<T>(k, v.t, v.g, s, &st->mv_t_on);
+    k_lin_alpha<T><<<c.rb, NTHREADS, 0, s>>>(v.t, v.g, C, part, tk, st, c.n);
+    k_lin_update<T><<<c.rb, NTHREADS, 0, s>>>(v.x, v.r, v.t, v.g, C, part, tk, st, c.n);
+    k_lin_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.r, v.t, C, st, c.n);
+    note_launches(3);
+  }
+}
+
+template <typename T>
+bem_status lin_chunk(bem_kernel_s* k, const uint8_t* C, cudaStream_t s) {
+  auto& gr = k->graphs;
+  if (gr.lin_exec != nullptr && gr.lin_mask != (const void*)C) {   // captured with another mask array
+    BEM_CUDA_TRY(cudaGraphExecDestroy(gr.lin_exec));
+    gr.lin_exec = nullptr;
+  }
+  gr.lin_mask = C;
+  return chunk_graph(k, s, gr.lin_exec, gr.lin_nodes, gr.lin_warm, [&] { lin_chunk_launches<T>(k, C, s); });
 }
 
 template <typename T>
@@ -888,17 +924,9 @@ bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit
     note_launches(1);
     mv += 1;
     for (;;) {
-      for (int it = 0; it < CHUNK; ++it) {
-        launch_matvec<T>(k, v.t, v.g, s, &st->mv_t_on);
-        k_lin_alpha<T><<<c.rb, NTHREADS, 0, s>>>(v.t, v.g, C, part, tk, st, c.n);
-        note_launches(1);
-        k_lin_update<T><<<c.rb, NTHREADS, 0, s>>>(v.x, v.r, v.t, v.g, C, part, tk, st, c.n);
-        note_launches(1);
-        k_lin_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.r, v.t, C, st, c.n);
-        note_launches(1);
-      }
-      BEM_CUDA_TRY(cudaGetLastError());
-      bem_status e = read_state<T>(k, s);
+      bem_status e = lin_chunk<T>(k, C, s);
+      if (e != BEM_OK) return e;
+      e = read_state<T>(k, s);
       if (e != BEM_OK) return e;
       if (hs->done) break;
     }

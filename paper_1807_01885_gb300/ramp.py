@@ -20,7 +20,16 @@ def run(kernel, height, depths, dgamma, tol=1e-8, max_iter=20000, state=None, ch
         stream=None):
     """Runs the ramp; returns a list of per-step records (d, force, area, a_eq, n_contact,
     iterations, outer iterations, status).  ``state`` = (step, p, mask) resumes a saved
-    ramp; ``checkpoint`` is a path for np.savez every ``every`` steps."""
+    ramp; ``checkpoint`` is a path for np.savez every ``every`` steps.  The solves run
+    on ``stream`` (default: a stream of the ramp's own, on which the library replays
+    its captured iteration graphs; every solve synchronises its stream)."""
+    if stream is None:
+        stream = torch.cuda.Stream(device=height.device)
+    with torch.cuda.stream(stream):
+        return _run(kernel, height, depths, dgamma, tol, max_iter, state, checkpoint, every, stream)
+
+
+def _run(kernel, height, depths, dgamma, tol, max_iter, state, checkpoint, every, stream):
     N = kernel.N
     dev = height.device
     if state is None:

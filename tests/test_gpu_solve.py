@@ -240,3 +240,34 @@ def test_graph_replay_equals_plain_launches(cuda):
         s.synchronize()
     for p1, r1 in outs:
         assert torch.equal(p0, p1) and r0["iters"] == r1["iters"]
+
+
+def test_adhesive_graph_replay_equals_plain_launches(cuda):
+    """An adhesive solve on a non-default stream replays the handle's captured
+    linear-CG chunk; contact areas, pressures and iteration counts equal those of the
+    plain launches on the default stream."""
+    N, R, E, nu = 64, 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Es = E / (1 - nu * nu)
+    dg = (5 * delta) ** 3 * 8 * Es / (np.pi * R * R)
+    f = inputs.sphere_height(N, delta, R)
+    depths = [0.004, 0.008, 0.002, -0.002]
+    runs = []
+    for use_stream in (False, True, True):
+        with bem.Kernel(N, delta, np.inf, E, nu, E, nu, precision="fp32") as k:
+            ft = torch.tensor(f, device=cuda, dtype=torch.float32)
+            s = torch.cuda.Stream() if use_stream else None
+            mask = torch.zeros((N, N), dtype=torch.uint8, device=cuda)
+            p = torch.zeros_like(ft)
+            rec = []
+            for d in depths:
+                p, res = k.solve(ft, "depth", d, dgamma=dg, tol=1e-7, p_init=p, contact_mask=mask, stream=s)
+                if s is not None:
+                    s.synchronize()
+                p = p.clone()
+                rec.append((p, mask.clone(), res["iters"], res["outer_iters"], res["status"]))
+            runs.append(rec)
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert a[4] == 0 and b[4] == 0
+            assert torch.equal(a[1], b[1]) and torch.equal(a[0], b[0]) and a[2:4] == b[2:4]
