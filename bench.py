@@ -13,7 +13,9 @@ once per instance before timing.
 value = operator products per second over the whole job (all ranks); the step
 time is the time to converge.  Extra keys: matvec-only throughput on 8 distinct
 inputs (larger than L2), the roofline of the dominant pass, the end-to-end number
-through the C ABI with host buffers, and the CPU oracle timed on a bounded sample.
+through the C ABI with host buffers, the CPU oracle timed on a bounded sample, the
+256-instance batch of uneven grids (batched vs one after another), the adhesive
+ramp (200 displacement steps at N = 512) and the learned warm start.
 
 --impl reference times the CPU FP64 oracle (the method written plainly, see
 oracle/) on the same workload: each step is one N = 2048 operator product.
@@ -50,6 +52,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="instances of the batch workload (0: skip)")
     ap.add_argument("--warmstart", type=int, default=512,
                     help="training solutions for the learned warm start (0: skip)")
+    ap.add_argument("--adhesive", type=int, default=1,
+                    help="run the adhesive ramp workload (N=512, 200 steps, FP32; 0: skip)")
     ap.add_argument("--radix", default=None, metavar="ROWS,COLS",
                     help="log2 FFT radices to use instead of the autotuner's choice (e.g. 4,4); for "
                          "profiling runs, where the autotuner's timings would be taken under the profiler")
@@ -248,6 +252,39 @@ def batch_bench(torch, dev, bem, inputs, n_inst, radix):
             "matvecs": mv, "matvecs_per_s": mv / t_batch,
             "fft_log2_radix": {str(n): list(radix.choice[n]) for n in sorted(sizes)},
             "seeds": f"{BATCH_SEED0}..{BATCH_SEED0 + n_inst - 1}"}
+
+
+def adhesive_bench(torch, dev, bem, inputs):
+    """Adhesive ramp (Sec. 2 procedure, Eq. 12): sphere R = 1 on a coating E1 = 0.2,
+    h = a_max/2, over E2 = 1, nu = 0.3; N = 512, L = 4 a_max with a_max = 0.1; the work
+    of adhesion from a Tabor parameter of 5 with z0 = delta; 100 loading steps to
+    d_max = a_max^2/R, then 100 unloading steps to -d_max; FP32, tol 1e-7.  Timed on
+    one stream (the ramp driver's own): wall time of the 200 steps."""
+    from paper_1807_01885_gb300 import ramp
+    N, R, E1, E2, nu = 512, 1.0, 0.2, 1.0, 0.3
+    a_max = 0.1
+    delta = 4 * a_max / N
+    h = 0.5 * a_max
+    E1s = E1 / (1 - nu * nu)
+    mu = 5.0
+    dg = E1s * np.sqrt(mu ** 3 * delta ** 3 / R)
+    d_max = a_max ** 2 / R
+    f = torch.tensor(inputs.sphere_height(N, delta, R), device=dev, dtype=torch.float32)
+    depths = np.concatenate([np.linspace(0, d_max, 101)[1:], np.linspace(d_max, -d_max, 101)[1:]])
+    s = torch.cuda.Stream(device=dev)
+    with bem.Kernel(N, delta, h, E1, nu, E2, nu, precision="fp32") as k:
+        ramp.run(k, f, depths[:5], dg, tol=1e-7, stream=s)              # graph capture, warm caches
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ramp.run(k, f, depths, dg, tol=1e-7, stream=s)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"N": N, "steps": len(depths), "wall_s": dt, "ms_per_step": 1000 * dt / len(depths),
+            "cg_iters": int(sum(r["iters"] for r in out)), "outer_passes": int(sum(r["outer"] for r in out)),
+            "pull_off_force": float(min(r["force"] for r in out)),
+            "all_converged": all(r["status"] == 0 for r in out),
+            "contact_lost_after_step": int(max([i for i, r in enumerate(out) if r["n_contact"] > 0], default=-1)),
+            "dtype": "f32", "tabor": mu}
 
 
 WS_TRAIN_SEED0 = 30000000
@@ -502,6 +539,8 @@ def run_ours(args):
     }
     if args.batch > 0:
         line["batch"] = batch_bench(torch, dev, bem, inputs, args.batch, radix)
+    if args.adhesive > 0:
+        line["adhesive_ramp"] = adhesive_bench(torch, dev, bem, inputs)
     if args.warmstart > 0:
         line["warm_start"] = warm_start_bench(torch, dev, bem, args.warmstart, 1500, 2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
