@@ -338,8 +338,32 @@ def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
         _, r_warm = warmstart.solve_all(test, heights, p_init=p_init, stream=s)
         s.synchronize()
         t_warm = time.perf_counter() - t0
+        # the same at the training resolution: 32 held-out N = 256 instances, batched
+        small = warmstart.default_instances(32, 256, WS_TEST_SEED0)
+        hs, ps, pbs = warmstart.instance_tensors(small, dev)
+        warmstart.solve_all(small, hs, stream=s)
+        s.synchronize()
+        t0 = time.perf_counter()
+        _, rs_cold = warmstart.solve_all(small, hs, stream=s)
+        s.synchronize()
+        ts_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ps_init = warmstart.predict(net, hs, ps, pbs)
+        torch.cuda.synchronize()
+        ts_pred = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, rs_warm = warmstart.solve_all(small, hs, p_init=ps_init, stream=s)
+        s.synchronize()
+        ts_warm = time.perf_counter() - t0
     net.close()
+    at_train_res = {"N": 256, "instances": len(small), "seeds": f"{WS_TEST_SEED0}..{WS_TEST_SEED0 + len(small) - 1}",
+                    "cold_iters_mean": float(np.mean([r["iters"] for r in rs_cold])),
+                    "warm_iters_mean": float(np.mean([r["iters"] for r in rs_warm])),
+                    "cold_batch_ms": 1000 * ts_cold, "warm_batch_ms": 1000 * ts_warm,
+                    "inference_ms": 1000 * ts_pred,
+                    "all_converged": all(r["status"] == 0 for r in rs_cold + rs_warm)}
     return {"train_samples": n_train, "train_N": 256, "train_steps": steps, "batch": 8,
+            "q_min": 1.0, "at_training_resolution": at_train_res,
             "data_s": t_data, "train_s": t_train,
             "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
             "test_N": N_GRID, "test_instances": n_test, "test_seeds": f"{WS_TEST_SEED0}..{WS_TEST_SEED0 + n_test - 1}",

@@ -237,9 +237,12 @@ bem_status bem_fno_train_step(bem_fno f, int32_t B, int32_t N, const float* x, c
 /* training target q = p / pbar[b] (pbar: B doubles, device) */
 bem_status bem_fno_target(bem_fno f, int32_t B, int32_t N, const float* p, const double* pbar, float* q,
                           void* cuda_stream);
-/* warm-start pressure p = pbar[b] * max(out, 0) (pbar: B doubles, device) */
-bem_status bem_fno_pressure(bem_fno f, int32_t B, int32_t N, const float* out, const double* pbar, float* p,
-                            void* cuda_stream);
+/* warm-start pressure p = pbar[b] * out where out > q_min, 0 elsewhere (pbar: B
+ * doubles, device; q_min >= 0).  q_min = 0 keeps every cell the network puts in
+ * contact; a larger cut keeps only its confident cells (q_min = 1: above the mean
+ * pressure), which starts the solve from a sparser contact set. */
+bem_status bem_fno_pressure(bem_fno f, int32_t B, int32_t N, const float* out, const double* pbar, float q_min,
+                            float* p, void* cuda_stream);
 
 /* Number of kernel launches the library has issued since it was loaded. */
 int64_t bem_launch_count(void);

@@ -111,7 +111,7 @@ def load(path=None):
     lib.bem_fno_gradients.argtypes = [vp, i32, i32, vp, vp, vp, dbl, vp]
     lib.bem_fno_train_step.argtypes = [vp, i32, i32, vp, vp, ctypes.c_float, dbl, vp]
     lib.bem_fno_target.argtypes = [vp, i32, i32, vp, vp, vp, vp]
-    lib.bem_fno_pressure.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    lib.bem_fno_pressure.argtypes = [vp, i32, i32, vp, vp, ctypes.c_float, vp, vp]
     for name in ("bem_fno_create", "bem_fno_destroy", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features",
                  "bem_fno_forward", "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure"):
         getattr(lib, name).restype = i32
@@ -365,8 +365,9 @@ class Fno:
         _check(load().bem_fno_target(self.handle, B, N, _ptr(p), _ptr(pbar), _ptr(q), _stream(stream)))
         return q
 
-    def pressure(self, B, N, out, pbar, p, stream=None):
-        _check(load().bem_fno_pressure(self.handle, B, N, _ptr(out), _ptr(pbar), _ptr(p), _stream(stream)))
+    def pressure(self, B, N, out, pbar, p, q_min=0.0, stream=None):
+        _check(load().bem_fno_pressure(self.handle, B, N, _ptr(out), _ptr(pbar), float(q_min), _ptr(p),
+                                       _stream(stream)))
         return p
 
     def close(self):

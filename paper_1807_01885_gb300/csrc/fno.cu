@@ -361,11 +361,11 @@ __global__ void k_bf16_to_f32(const bf16* __restrict__ wb, float* __restrict__ w
 }
 
 // p_init[b][p] = pbar[b] * max(out[b][p], 0)
-__global__ void k_fno_pressure(const float* __restrict__ out, const double* __restrict__ pbar, float* __restrict__ p,
-                               size_t P, int B) {
+__global__ void k_fno_pressure(const float* __restrict__ out, const double* __restrict__ pbar, float q_min,
+                               float* __restrict__ p, size_t P, int B) {
   FOR_N(i, (size_t)B * P) {
     const float q = out[i];
-    p[i] = q > 0.f ? (float)pbar[i / P] * q : 0.f;
+    p[i] = q > q_min ? (float)pbar[i / P] * q : 0.f;
   }
 }
 
@@ -777,14 +777,14 @@ bem_status bem_fno_train_step(bem_fno f, int32_t B, int32_t N, const float* x, c
   return BEM_OK;
 }
 
-bem_status bem_fno_pressure(bem_fno f, int32_t B, int32_t N, const float* out, const double* pbar, float* p,
-                            void* cuda_stream) {
-  if (f == nullptr || out == nullptr || pbar == nullptr || p == nullptr || B < 1) {
+bem_status bem_fno_pressure(bem_fno f, int32_t B, int32_t N, const float* out, const double* pbar, float q_min,
+                            float* p, void* cuda_stream) {
+  if (f == nullptr || out == nullptr || pbar == nullptr || p == nullptr || B < 1 || !(q_min >= 0.f)) {
     set_error("invalid FNO pressure arguments");
     return BEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  k_fno_pressure<<<blocks_for((size_t)B * N * N), FT, 0, s>>>(out, pbar, p, (size_t)N * N, B);
+  k_fno_pressure<<<blocks_for((size_t)B * N * N), FT, 0, s>>>(out, pbar, q_min, p, (size_t)N * N, B);
   note_launches(1);
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;

@@ -5,8 +5,9 @@ construction, network forward/backward/Adam, target and pressure scaling); this
 module moves device tensors between those calls and picks minibatches.
 
 The network predicts q = p / pbar (pbar = F / L^2, the mean pressure) from the height
-map and the layer parameters; the warm start handed to the solver is
-p_init = pbar max(q, 0), which the force-controlled solve then rescales to F exactly.
+map and the layer parameters; the warm start handed to the solver is p_init = pbar q
+on the cells where q exceeds a cut (1 by default: the network's confident contact
+cells), 0 elsewhere, which the force-controlled solve then rescales to F exactly.
 """
 import numpy as np
 import torch
@@ -76,16 +77,23 @@ def train(fno, x, q, steps, batch, lr, seed=0, lr_final=None):
     return losses
 
 
-def predict(fno, heights, params, pbar):
-    """Warm-start pressures p_init [B, N, N] for stacked instances."""
+# cells per network call in prediction (bounds the network's activation buffers)
+PREDICT_CELLS = 1 << 22
+
+
+def predict(fno, heights, params, pbar, q_min=1.0):
+    """Warm-start pressures p_init [B, N, N] for stacked instances: the network runs
+    on as many samples per call as PREDICT_CELLS allows; cells with q <= q_min get 0."""
     B, N = heights.shape[0], heights.shape[-1]
     x = torch.empty((B, 7, N, N), dtype=torch.float32, device=heights.device)
     fno.features(B, N, heights, params, x)
     out = torch.empty_like(heights)
     p = torch.empty_like(heights)
-    for b in range(B):
-        fno.forward(1, N, x[b:b + 1], out[b:b + 1])
-    fno.pressure(B, N, out, pbar, p)
+    step = max(1, PREDICT_CELLS // (N * N))
+    for b0 in range(0, B, step):
+        b1 = min(B, b0 + step)
+        fno.forward(b1 - b0, N, x[b0:b1], out[b0:b1])
+    fno.pressure(B, N, out, pbar, p, q_min=q_min)
     return p
 
 
