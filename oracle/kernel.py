@@ -8,7 +8,8 @@ Test infrastructure (see ``oracle/__init__``).  Plain FP64 numpy.
   factor (E2(1+nu1) + E1(1+nu2))^2, which cancels in Eq. (9); finite for E2 = inf.
 * ``khat_layered``       Eq. (9)/(11): the factor multiplying FFT(p).
 * ``khat_dc``            the k -> 0 finite part used for the zero wave number (the
-  paper's Eq. (11) is defined for k != 0 only; reading documented in the design doc).
+  paper's Eq. (11) is defined for k != 0 only, so the value at k = 0 is a reading:
+  the finite part lim_{k->0} [K^(k) - 2/(E2* k)]).
 * ``lam_rigid``          Eq. (25): Lambda(u), L = 4 nu - 3.
 * ``khat_transfer_matrix``  an independent derivation: Eq. (5) written as a
   first-order system in (u_k, u_z, sigma_kz, sigma_zz), propagated through the layer

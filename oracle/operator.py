@@ -4,8 +4,8 @@ Test infrastructure (see ``oracle/__init__``).  Plain FP64 numpy.
 
 Discretisation (Sec. 2, Fig. 2): an N x N window of square cells of side delta,
 row-major, row index r along y and column index c along x; the pressure is
-uniform per cell.  Reading of Eq. (11) used here (documented in the design doc): the
-window is embedded in an M x M period with M = 2N (zero pressure outside the
+uniform per cell.  Reading of Eq. (11) used here (the paper states the periodic
+form only): the window is embedded in an M x M period with M = 2N (zero pressure outside the
 window), the compliance of Eq. (9) is sampled on that period's wave-number grid
 k = 2 pi (i~, j~)/(M delta) with i~ = i for i <= N and i - M otherwise, the k = 0
 term takes the finite part of ``kernel.khat_dc`` (or 0 with dc_mode=1, the literal
