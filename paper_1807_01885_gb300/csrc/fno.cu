@@ -163,10 +163,6 @@ __global__ void k_gelu_bwd(const float* __restrict__ dv, const float* __restrict
   FOR_N(i, n) dz[i] = dv[i] * gelu_grad_f(z[i]);
 }
 
-__global__ void k_gelu_fwd(const float* __restrict__ z, float* __restrict__ v, size_t n) {
-  FOR_N(i, n) v[i] = gelu_f(z[i]);
-}
-
 // ---------------------------------------------------------------------------
 // truncated transforms; tw[k] = e^{-2 pi i k / N}
 
