@@ -40,11 +40,18 @@ int blocks_for(size_t n) { return (int)std::min<size_t>((n + FT - 1) / FT, 65535
 // ---------------------------------------------------------------------------
 // inputs
 
-// per-sample mean and standard deviation of the height map (one block per sample)
-__global__ void k_fno_moments(const float* __restrict__ f, float* __restrict__ mom, size_t P) {
-  const float* fb = f + blockIdx.x * P;
-  double s = 0.0, s2 = 0.0;   // a few values per thread, once per call
-  for (size_t i = threadIdx.x; i < P; i += blockDim.x) {
+// per-sample mean and standard deviation of the height map: kMomChunks blocks per
+// sample add the values and squares of their chunk in double (a few per thread,
+// spread over the whole GPU: double arithmetic runs at a fraction of the float
+// rate), then one block per sample adds its chunk sums in chunk order
+constexpr int kMomChunks = 64;
+
+__global__ void k_fno_moments_part(const float* __restrict__ f, double* __restrict__ part, size_t P) {
+  const int b = blockIdx.y, ch = blockIdx.x;
+  const size_t lo = P * ch / kMomChunks, hi = P * (ch + 1) / kMomChunks;
+  const float* fb = f + (size_t)b * P;
+  double s = 0.0, s2 = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const double v = fb[i];
     s += v;
     s2 += v * v;
@@ -61,11 +68,23 @@ __global__ void k_fno_moments(const float* __restrict__ f, float* __restrict__ m
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double mean = sh[0][0] / (double)P;
-    const double var = fmax(sh[1][0] / (double)P - mean * mean, 1e-30);
-    mom[2 * blockIdx.x] = (float)mean;
-    mom[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var));
+    part[((size_t)b * kMomChunks + ch) * 2] = sh[0][0];
+    part[((size_t)b * kMomChunks + ch) * 2 + 1] = sh[1][0];
   }
+}
+
+__global__ void k_fno_moments(const double* __restrict__ part, float* __restrict__ mom, size_t P) {
+  if (threadIdx.x != 0) return;
+  const double* pb = part + (size_t)blockIdx.x * kMomChunks * 2;
+  double s = 0.0, s2 = 0.0;
+  for (int ch = 0; ch < kMomChunks; ++ch) {
+    s += pb[2 * ch];
+    s2 += pb[2 * ch + 1];
+  }
+  const double mean = s / (double)P;
+  const double var = fmax(s2 / (double)P - mean * mean, 1e-30);
+  mom[2 * blockIdx.x] = (float)mean;
+  mom[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var));
 }
 
 // x[b][0] = normalised height, [1] = log(h/delta)/log 200, [2] = log(E1/E2)/log 20,
@@ -168,50 +187,7 @@ __global__ void k_gelu_bwd(const float* __restrict__ dv, const float* __restrict
 
 __device__ __forceinline__ int kx_of(int kxi, int m, int N) { return kxi < m ? kxi : N - 2 * m + kxi; }
 
-// A[row][ky] = sum_y v[row][y] e^{-2 pi i ky y/N},  ky < m
-__global__ void k_dft_y(const float* __restrict__ v, float2* __restrict__ A, const float2* __restrict__ tw, int N,
-                        int m, size_t rows) {
-  FOR_N(i, rows * m) {
-    const size_t row = i / m;
-    const int ky = (int)(i % m);
-    const float* vr = v + row * N;
-    float re = 0.f, im = 0.f;
-    int idx = 0;
-    for (int y = 0; y < N; ++y) {
-      const float2 w = tw[idx];
-      re = fmaf(vr[y], w.x, re);
-      im = fmaf(vr[y], w.y, im);
-      idx += ky;
-      if (idx >= N) idx -= N;
-    }
-    A[i] = make_float2(re, im);
-  }
-}
 
-// Xh[bc][kxi][ky] = wky[ky] * sum_x A[bc][x][ky] e^{-2 pi i kx x/N}   (wky may be null)
-__global__ void k_dft_x(const float2* __restrict__ A, float2* __restrict__ Xh, const float2* __restrict__ tw,
-                        const float* __restrict__ wky, int N, int m, size_t bc) {
-  const int nm = 2 * m * m;
-  FOR_N(i, bc * nm) {
-    const size_t q = i / nm;
-    const int mode = (int)(i % nm);
-    const int kxi = mode / m, ky = mode % m;
-    const int kx = kx_of(kxi, m, N);
-    const float2* a = A + q * (size_t)N * m + ky;
-    float re = 0.f, im = 0.f;
-    int idx = 0;
-    for (int x = 0; x < N; ++x) {
-      const float2 w = tw[idx];
-      const float2 v = a[(size_t)x * m];
-      re += v.x * w.x - v.y * w.y;
-      im += v.x * w.y + v.y * w.x;
-      idx += kx;
-      if (idx >= N) idx -= N;
-    }
-    const float s = wky != nullptr ? wky[ky] : 1.f;
-    Xh[i] = make_float2(re * s, im * s);
-  }
-}
 
 // A[bc][x][ky] = sum_kxi Y[bc][kxi][ky] e^{+2 pi i kx x/N}
 __global__ void k_idft_x(const float2* __restrict__ Y, float2* __restrict__ A, const float2* __restrict__ tw, int N,
@@ -233,27 +209,184 @@ __global__ void k_idft_x(const float2* __restrict__ Y, float2* __restrict__ A, c
   }
 }
 
-// out[row][y] (=|+=) scale * sum_ky c[ky] Re(A[row][ky] e^{+2 pi i ky y/N})   (c may be null: 1)
-template <bool ACCUM>
-__global__ void k_idft_y(const float2* __restrict__ A, float* __restrict__ out, const float2* __restrict__ tw,
-                         const float* __restrict__ c, float scale, int N, int m, size_t rows) {
-  FOR_N(i, rows * N) {
-    const size_t row = i / N;
-    const int y = (int)(i % N);
-    const float2* a = A + row * m;
-    float acc = 0.f;
-    int idx = 0;
-    for (int ky = 0; ky < m; ++ky) {
-      const float2 w = tw[idx];   // e^{-i ky y theta}
-      const float2 v = a[ky];
-      const float re = v.x * w.x + v.y * w.y;   // Re(v conj(w))
-      acc = fmaf(c != nullptr ? c[ky] : 1.f, re, acc);
-      idx += y;
-      if (idx >= N) idx -= N;
+
+// Truncated transforms along y as matrix products (FP32, register-blocked tiles in
+// shared memory).  Tf[y][2k] + i Tf[y][2k+1] = e^{-2 pi i k y / N} (k < m) and
+// Ti[2k + e][y] = Tf[y][2k + e]: the forward transform of every row is A = V Tf,
+// the inverse out[y] = sum_k c_k Re(A_k conj(w_k(y))) is (A diag(c)) Ti.
+__global__ void k_twiddle_mats(const float2* __restrict__ tw, float* __restrict__ Tf, float* __restrict__ Ti, int N,
+                               int m) {
+  FOR_N(i, (size_t)N * m) {
+    const int y = (int)(i / m), k = (int)(i % m);
+    const float2 w = tw[((size_t)k * y) % N];
+    Tf[(size_t)y * 2 * m + 2 * k] = w.x;
+    Tf[(size_t)y * 2 * m + 2 * k + 1] = w.y;
+    Ti[(size_t)(2 * k) * N + y] = w.x;
+    Ti[(size_t)(2 * k + 1) * N + y] = w.y;
+  }
+}
+
+// c_k / N^2, the weights of the gradient of the inverse transform, for the current N
+__global__ void k_cky_scaled(const float* __restrict__ c, float* __restrict__ cs, int m, float inv) {
+  FOR_N(k, (size_t)m) cs[k] = c[k] * inv;
+}
+
+constexpr int G1_BM = 128, G1_BN = 32, G1_BK = 32;   // forward: 256 threads, 4 x 4 outputs each
+// C[r][j] = sum_y V[r][y] Tf[y][j] for rows r < rows, j < n2m (= 2m)
+__global__ void __launch_bounds__(256) k_dft_y_gemm(const float* __restrict__ V, const float* __restrict__ Tf,
+                                                    float* __restrict__ C, size_t rows, int N, int n2m) {
+  __shared__ __align__(16) float Vs[G1_BK][G1_BM + 4];
+  __shared__ __align__(16) float Ts[G1_BK][G1_BN];
+  const int tid = threadIdx.x;
+  const size_t r0 = (size_t)blockIdx.x * G1_BM;
+  const int c0 = blockIdx.y * G1_BN;
+  const int tr = (tid / 8) * 4, tc = (tid % 8) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < N; k0 += G1_BK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {   // V tile, 128 rows x 32 k, stored k-major
+      const int f = tid + 256 * q, row = f / 8, kq = (f % 8) * 4;
+      const size_t r = r0 + row;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = k0 + kq + e;
+        Vs[kq + e][row] = (r < rows && k < N) ? V[r * N + k] : 0.f;
+      }
     }
-    acc *= scale;
-    if (ACCUM) out[i] += acc;
-    else out[i] = acc;
+    {   // Tf tile, 32 k x 32 columns
+      const int k = tid / 8, cq = (tid % 8) * 4;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = c0 + cq + e;
+        Ts[k][cq + e] = (k0 + k < N && col < n2m) ? Tf[(size_t)(k0 + k) * n2m + col] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < G1_BK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&Vs[kk][tr]);
+      const float4 b = *reinterpret_cast<const float4*>(&Ts[kk][tc]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const size_t r = r0 + tr + i;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + tc + j;
+      if (col < n2m) C[r * n2m + col] = acc[i][j];
+    }
+  }
+}
+
+constexpr int G2_BM = 64, G2_BN = 128, G2_BK = 32;   // inverse: 256 threads, 4 x 8 outputs each
+// out[r][y] (+)= sum_k A[r][k] cs(k) Ti[k][y], k < n2m, cs(k) = scale * (c ? c[k/2] : 1)
+template <bool ACCUM>
+__global__ void __launch_bounds__(256) k_idft_y_gemm(const float* __restrict__ A, const float* __restrict__ Ti,
+                                                     const float* __restrict__ c, float scale,
+                                                     float* __restrict__ out, size_t rows, int N, int n2m) {
+  __shared__ float As[G2_BK][G2_BM + 1];
+  __shared__ __align__(16) float Us[G2_BK][G2_BN];
+  const int tid = threadIdx.x;
+  const size_t r0 = (size_t)blockIdx.x * G2_BM;
+  const int c0 = blockIdx.y * G2_BN;
+  const int tr = (tid / 16) * 4, tc = (tid % 16) * 8;
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < n2m; k0 += G2_BK) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {   // A tile, 64 rows x 32 k (scaled), stored k-major
+      const int f = tid + 256 * q, row = f / 32, k = f % 32;
+      const size_t r = r0 + row;
+      const int kg = k0 + k;
+      float val = 0.f;
+      if (r < rows && kg < n2m) val = A[r * n2m + kg] * (scale * (c != nullptr ? c[kg / 2] : 1.f));
+      As[k][row] = val;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {  // Ti tile, 32 k x 128 y
+      const int f = tid + 256 * q, k = f / 128, cc = f % 128;
+      const int y = c0 + cc;
+      Us[k][cc] = (k0 + k < n2m && y < N) ? Ti[(size_t)(k0 + k) * N + y] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < G2_BK; ++kk) {
+      float av[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][tr + i];
+      const float4 b0 = *reinterpret_cast<const float4*>(&Us[kk][tc]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Us[kk][tc + 4]);
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const size_t r = r0 + tr + i;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int y = c0 + tc + j;
+      if (y < N) {
+        float* o = out + r * N + y;
+        if (ACCUM) *o += acc[i][j];
+        else *o = acc[i][j];
+      }
+    }
+  }
+}
+
+// Xh[q][kxi][ky] = s[ky] sum_x A[q][x][ky] e^{-2 pi i kx x/N}: block (q, kxi); thread
+// (slice, ky) adds every S-th x from its slice, then the slices are added in order
+__global__ void __launch_bounds__(256) k_dft_x_par(const float2* __restrict__ A, float2* __restrict__ Xh,
+                                                   const float2* __restrict__ tw, const float* __restrict__ wky,
+                                                   int N, int m) {
+  __shared__ float2 red[256];
+  const size_t q = blockIdx.x;
+  const int kxi = blockIdx.y;
+  const int kx = kx_of(kxi, m, N);
+  const int S = 256 / m;
+  const int ky = threadIdx.x % m, slice = threadIdx.x / m;
+  float re = 0.f, im = 0.f;
+  if (slice < S) {
+    const float2* a = A + q * (size_t)N * m + ky;
+    for (int x = slice; x < N; x += S) {
+      const float2 w = tw[((size_t)kx * x) % N];
+      const float2 v = a[(size_t)x * m];
+      re += v.x * w.x - v.y * w.y;
+      im += v.x * w.y + v.y * w.x;
+    }
+  }
+  red[threadIdx.x] = make_float2(re, im);
+  __syncthreads();
+  if (threadIdx.x < m) {
+    float2 t = red[threadIdx.x];
+    for (int sl = 1; sl < S; ++sl) {
+      const float2 u = red[sl * m + threadIdx.x];
+      t.x += u.x;
+      t.y += u.y;
+    }
+    const float sc = wky != nullptr ? wky[threadIdx.x] : 1.f;
+    Xh[(q * 2 * m + kxi) * m + threadIdx.x] = make_float2(t.x * sc, t.y * sc);
   }
 }
 
@@ -402,9 +535,12 @@ struct bem_fno_s {
   std::vector<float2*> Xh;
   float *a = nullptr, *h = nullptr, *out = nullptr, *dout = nullptr;
   float *dv = nullptr, *dz = nullptr, *dt = nullptr, *mom = nullptr, *part = nullptr, *cky = nullptr, *cky_s = nullptr;
+  double* mom_part = nullptr;   // per-chunk sums of the height moments
   float2 *A = nullptr, *Y = nullptr, *dY = nullptr, *tw = nullptr;
+  float *Tf = nullptr, *Ti = nullptr;   // twiddle matrices of the y transforms (N x 2m, 2m x N)
   double* lpart = nullptr;
   std::vector<void*> owned;
+  size_t n_persistent = 0;   // leading entries of owned that live as long as the handle
 };
 
 namespace {
@@ -417,24 +553,30 @@ cudaError_t alloc(bem_fno_s* f, P** p, size_t count) {
 }
 
 constexpr int kMaxSamples = 4096;
-constexpr size_t kPersistent = 6;   // parameters, optimiser state and moments come first in owned
-
+// frees the activation buffers: everything allocated after the handle's persistent
+// buffers (parameters, optimiser state, moments), whose count is recorded at creation
 void free_acts(bem_fno_s* f) {
-  for (size_t i = kPersistent; i < f->owned.size(); ++i) cudaFree(f->owned[i]);
-  f->owned.resize(std::min<size_t>(f->owned.size(), kPersistent));
+  for (size_t i = f->n_persistent; i < f->owned.size(); ++i) cudaFree(f->owned[i]);
+  f->owned.resize(std::min<size_t>(f->owned.size(), f->n_persistent));
   f->v.clear();
   f->z.clear();
   f->Xh.clear();
   f->capB = f->capN = f->twN = 0;
 }
 
+// twiddles, the y-transform matrices and the gradient weights c_k / N^2 for grid N
+void set_twiddles(bem_fno_s* f, int N, cudaStream_t s) {
+  const int m = f->d.modes;
+  k_twiddle_f<<<blocks_for(N), FT, 0, s>>>(f->tw, N);
+  k_twiddle_mats<<<blocks_for((size_t)N * m), FT, 0, s>>>(f->tw, f->Tf, f->Ti, N, m);
+  k_cky_scaled<<<1, 32, 0, s>>>(f->cky, f->cky_s, m, (float)(1.0 / ((double)N * N)));
+  note_launches(3);
+  f->twN = N;
+}
+
 bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
   if (B <= f->capB && N <= f->capN && (!train || f->cap_train)) {
-    if (f->twN != N) {
-      k_twiddle_f<<<blocks_for(N), FT, 0, s>>>(f->tw, N);
-      note_launches(1);
-      f->twN = N;
-    }
+    if (f->twN != N) set_twiddles(f, N, s);
     return BEM_OK;
   }
   free_acts(f);
@@ -461,6 +603,8 @@ bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
   if (e == cudaSuccess) e = alloc(f, &f->Y, (size_t)B * W * nm);
   if (e == cudaSuccess) e = alloc(f, &f->dY, (size_t)B * W * nm);
   if (e == cudaSuccess) e = alloc(f, &f->tw, (size_t)N);
+  if (e == cudaSuccess) e = alloc(f, &f->Tf, (size_t)2 * m * N);
+  if (e == cudaSuccess) e = alloc(f, &f->Ti, (size_t)2 * m * N);
   const size_t nblk = (size_t)B * ((P + FT - 1) / FT);
   const size_t maxout = (size_t)std::max(W, H) * std::max({W, H, 7}) + std::max(W, H);
   if (e == cudaSuccess && train) e = alloc(f, &f->part, nblk * maxout);
@@ -474,17 +618,11 @@ bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
   f->capB = B;
   f->capN = N;
   f->cap_train = train;
-  std::vector<float> c(m), cs(m);
-  for (int k = 0; k < m; ++k) {
-    c[k] = k == 0 ? 1.f : 2.f;
-    cs[k] = c[k] / (float)((double)N * N);
-  }
+  std::vector<float> c(m);
+  for (int k = 0; k < m; ++k) c[k] = k == 0 ? 1.f : 2.f;
   BEM_CUDA_TRY(cudaMemcpyAsync(f->cky, c.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
-  BEM_CUDA_TRY(cudaMemcpyAsync(f->cky_s, cs.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
   BEM_CUDA_TRY(cudaStreamSynchronize(s));
-  k_twiddle_f<<<blocks_for(N), FT, 0, s>>>(f->tw, N);
-  note_launches(1);
-  f->twN = N;
+  set_twiddles(f, N, s);
   return BEM_OK;
 }
 
@@ -524,16 +662,32 @@ void wgrad(const float* dY, int cout, const float* X, int cin, float* gw, float*
 }
 
 // spectral branch: out (=|+=) idft( R * dft(vin) ), caching dft(vin) in Xh
+// A (rows x m complex) = truncated DFT along y of the rows of v
+void dft_y(bem_fno_s* f, const float* v, size_t rows, int N, cudaStream_t s) {
+  const int n2m = 2 * f->d.modes;
+  const dim3 grid((unsigned)((rows + G1_BM - 1) / G1_BM), (unsigned)((n2m + G1_BN - 1) / G1_BN));
+  k_dft_y_gemm<<<grid, 256, 0, s>>>(v, f->Tf, reinterpret_cast<float*>(f->A), rows, N, n2m);
+}
+
+// out (rows x N) (+)= inverse truncated transform along y of A with weights c, scale
+template <bool ACCUM>
+void idft_y(bem_fno_s* f, float* out, const float* c, float scale, size_t rows, int N, cudaStream_t s) {
+  const int n2m = 2 * f->d.modes;
+  const dim3 grid((unsigned)((rows + G2_BM - 1) / G2_BM), (unsigned)((N + G2_BN - 1) / G2_BN));
+  k_idft_y_gemm<ACCUM><<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(f->A), f->Ti, c, scale, out, rows, N,
+                                            n2m);
+}
+
 void spectral_fwd(bem_fno_s* f, int l, const float* vin, float2* Xh, float* out, int B, int N, cudaStream_t s) {
   const int W = f->d.width, m = f->d.modes;
   const size_t bc = (size_t)B * W, nm = 2 * (size_t)m * m;
-  k_dft_y<<<blocks_for(bc * N * m), FT, 0, s>>>(vin, f->A, f->tw, N, m, bc * N);
-  k_dft_x<<<blocks_for(bc * nm), FT, 0, s>>>(f->A, Xh, f->tw, nullptr, N, m, bc);
+  dft_y(f, vin, bc * N, N, s);
+  k_dft_x_par<<<dim3((unsigned)bc, 2 * m), 256, 0, s>>>(f->A, Xh, f->tw, nullptr, N, m);
   const bf16* Rre = f->wb + f->o_Rre + (size_t)l * W * W * nm;
   const bf16* Rim = f->wb + f->o_Rim + (size_t)l * W * W * nm;
   k_mix<<<blocks_for(bc * nm), FT, 0, s>>>(Xh, Rre, Rim, f->Y, W, (int)nm, B);
   k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
-  k_idft_y<false><<<blocks_for(bc * N * N), FT, 0, s>>>(f->A, out, f->tw, f->cky, 1.f / ((float)N * N), N, m, bc * N);
+  idft_y<false>(f, out, f->cky, 1.f / ((float)N * N), bc * N, N, s);
   note_launches(5);
 }
 
@@ -589,8 +743,8 @@ bem_status backward(bem_fno_s* f, int B, int N, const float* x, const float* tar
     // pointwise branch of d_vin into dt
     pw<true, false, false>(dz, W, f->wb + f->o_Ww + (size_t)l * W * W, nullptr, f->dt, nullptr, W, P, B, s);
     // spectral branch: dY = (c/N^2) dft(dz); dR = sum_b conj(Xh) dY; dXh = sum_o conj(R) dY
-    k_dft_y<<<blocks_for(bc * N * m), FT, 0, s>>>(dz, f->A, f->tw, N, m, bc * N);
-    k_dft_x<<<blocks_for(bc * nm), FT, 0, s>>>(f->A, f->dY, f->tw, f->cky_s, N, m, bc);
+    dft_y(f, dz, bc * N, N, s);
+    k_dft_x_par<<<dim3((unsigned)bc, 2 * m), 256, 0, s>>>(f->A, f->dY, f->tw, f->cky_s, N, m);
     const bf16* Rre = f->wb + f->o_Rre + (size_t)l * W * W * nm;
     const bf16* Rim = f->wb + f->o_Rim + (size_t)l * W * W * nm;
     k_mix_wgrad<<<blocks_for((size_t)W * W * nm), FT, 0, s>>>(f->Xh[l], f->dY, f->g + f->o_Rre + (size_t)l * W * W * nm,
@@ -598,7 +752,7 @@ bem_status backward(bem_fno_s* f, int B, int N, const float* x, const float* tar
     k_mix_dgrad<<<blocks_for(bc * nm), FT, 0, s>>>(f->dY, Rre, Rim, f->Y, W, (int)nm, B);
     // d_vin += Re(sum dXh e^{+i theta}) (adjoint of the forward transform)
     k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
-    k_idft_y<true><<<blocks_for(bc * N * N), FT, 0, s>>>(f->A, f->dt, f->tw, nullptr, 1.f, N, m, bc * N);
+    idft_y<true>(f, f->dt, nullptr, 1.f, bc * N, N, s);
     note_launches(6);
     std::swap(f->dv, f->dt);
   }
@@ -655,6 +809,8 @@ bem_status bem_fno_create(const bem_fno_desc* desc, bem_fno* out) {
   if (e == cudaSuccess) e = alloc(f, &f->m1, f->P);
   if (e == cudaSuccess) e = alloc(f, &f->m2, f->P);
   if (e == cudaSuccess) e = alloc(f, &f->mom, (size_t)2 * kMaxSamples);
+  if (e == cudaSuccess) e = alloc(f, &f->mom_part, (size_t)2 * kMomChunks * kMaxSamples);
+  f->n_persistent = f->owned.size();
   if (e != cudaSuccess) {
     for (void* p : f->owned) cudaFree(p);
     delete f;
@@ -717,9 +873,10 @@ bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* height
   if (B > kMaxSamples) { set_error("at most 4096 samples per feature call"); return BEM_EINVAL; }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t P = (size_t)N * N;
-  k_fno_moments<<<B, FT, 0, s>>>(heights, f->mom, P);
+  k_fno_moments_part<<<dim3(kMomChunks, B), FT, 0, s>>>(heights, f->mom_part, P);
+  k_fno_moments<<<B, 32, 0, s>>>(f->mom_part, f->mom, P);
   k_fno_features<<<blocks_for((size_t)B * P), FT, 0, s>>>(heights, f->mom, params, x, N, B);
-  note_launches(2);
+  note_launches(3);
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
