@@ -355,12 +355,35 @@ def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
         _, rs_warm = warmstart.solve_all(small, hs, p_init=ps_init, stream=s)
         s.synchronize()
         ts_warm = time.perf_counter() - t0
+        # the same instances solved one after another (latency, not throughput):
+        # cold, then prediction for all of them plus seeded solves
+        ks = [bem.Kernel(i["N"], i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"], precision="fp32")
+              for i in small]
+        outs = torch.empty_like(hs)
+        for kk, i, b in zip(ks, small, range(len(small))):       # graph capture
+            kk.solve(hs[b], "force", i["force"], tol=TOL, p_out=outs[b], stream=s)
+        s.synchronize()
+        t0 = time.perf_counter()
+        for kk, i, b in zip(ks, small, range(len(small))):
+            kk.solve(hs[b], "force", i["force"], tol=TOL, p_out=outs[b], stream=s)
+        s.synchronize()
+        tq_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pq = warmstart.predict(net, hs, ps, pbs)
+        for kk, i, b in zip(ks, small, range(len(small))):
+            kk.solve(hs[b], "force", i["force"], tol=TOL, p_init=pq[b], p_out=outs[b], stream=s)
+        s.synchronize()
+        tq_warm = time.perf_counter() - t0
+        for kk in ks:
+            kk.close()
     net.close()
     at_train_res = {"N": 256, "instances": len(small), "seeds": f"{WS_TEST_SEED0}..{WS_TEST_SEED0 + len(small) - 1}",
                     "cold_iters_mean": float(np.mean([r["iters"] for r in rs_cold])),
                     "warm_iters_mean": float(np.mean([r["iters"] for r in rs_warm])),
                     "cold_batch_ms": 1000 * ts_cold, "warm_batch_ms": 1000 * ts_warm,
                     "inference_ms": 1000 * ts_pred,
+                    "sequential_cold_ms": 1000 * tq_cold,
+                    "sequential_inference_plus_warm_ms": 1000 * tq_warm,
                     "all_converged": all(r["status"] == 0 for r in rs_cold + rs_warm)}
     return {"train_samples": n_train, "train_N": 256, "train_steps": steps, "batch": 8,
             "q_min": 1.0, "at_training_resolution": at_train_res,
