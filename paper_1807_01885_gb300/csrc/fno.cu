@@ -73,7 +73,9 @@ __global__ void k_fno_moments_part(const float* __restrict__ f, double* __restri
   }
 }
 
-__global__ void k_fno_moments(const double* __restrict__ part, float* __restrict__ mom, size_t P) {
+// mom[4b .. 4b+3] = mean, 1/std, log(h/delta)/log 200, log(E1/E2)/log 20 of sample b
+__global__ void k_fno_moments(const double* __restrict__ part, const double* __restrict__ sp,
+                              float* __restrict__ mom, size_t P) {
   if (threadIdx.x != 0) return;
   const double* pb = part + (size_t)blockIdx.x * kMomChunks * 2;
   double s = 0.0, s2 = 0.0;
@@ -83,8 +85,11 @@ __global__ void k_fno_moments(const double* __restrict__ part, float* __restrict
   }
   const double mean = s / (double)P;
   const double var = fmax(s2 / (double)P - mean * mean, 1e-30);
-  mom[2 * blockIdx.x] = (float)mean;
-  mom[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var));
+  float* mb = mom + 4 * (size_t)blockIdx.x;
+  mb[0] = (float)mean;
+  mb[1] = (float)(1.0 / sqrt(var));
+  mb[2] = (float)(log(sp[4 * blockIdx.x]) / log(200.0));
+  mb[3] = (float)(log(sp[4 * blockIdx.x + 1]) / log(20.0));
 }
 
 // x[b][0] = normalised height, [1] = log(h/delta)/log 200, [2] = log(E1/E2)/log 20,
@@ -97,9 +102,10 @@ __global__ void k_fno_features(const float* __restrict__ f, const float* __restr
     const size_t pix = i % P;
     const int r = (int)(pix / N), c = (int)(pix % N);
     float* xb = x + (size_t)b * 7 * P;
-    xb[pix] = (f[i] - mom[2 * b]) * mom[2 * b + 1];
-    xb[P + pix] = (float)(log(sp[4 * b]) / log(200.0));
-    xb[2 * P + pix] = (float)(log(sp[4 * b + 1]) / log(20.0));
+    const float* mb = mom + 4 * (size_t)b;
+    xb[pix] = (f[i] - mb[0]) * mb[1];
+    xb[P + pix] = mb[2];
+    xb[2 * P + pix] = mb[3];
     xb[3 * P + pix] = (float)sp[4 * b + 2];
     xb[4 * P + pix] = (float)sp[4 * b + 3];
     xb[5 * P + pix] = ((float)c + 0.5f) / (float)N;
@@ -808,7 +814,7 @@ bem_status bem_fno_create(const bem_fno_desc* desc, bem_fno* out) {
   if (e == cudaSuccess) e = alloc(f, &f->g, f->P);
   if (e == cudaSuccess) e = alloc(f, &f->m1, f->P);
   if (e == cudaSuccess) e = alloc(f, &f->m2, f->P);
-  if (e == cudaSuccess) e = alloc(f, &f->mom, (size_t)2 * kMaxSamples);
+  if (e == cudaSuccess) e = alloc(f, &f->mom, (size_t)4 * kMaxSamples);
   if (e == cudaSuccess) e = alloc(f, &f->mom_part, (size_t)2 * kMomChunks * kMaxSamples);
   f->n_persistent = f->owned.size();
   if (e != cudaSuccess) {
@@ -874,7 +880,7 @@ bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* height
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t P = (size_t)N * N;
   k_fno_moments_part<<<dim3(kMomChunks, B), FT, 0, s>>>(heights, f->mom_part, P);
-  k_fno_moments<<<B, 32, 0, s>>>(f->mom_part, f->mom, P);
+  k_fno_moments<<<B, 32, 0, s>>>(f->mom_part, params, f->mom, P);
   k_fno_features<<<blocks_for((size_t)B * P), FT, 0, s>>>(heights, f->mom, params, x, N, B);
   note_launches(3);
   BEM_CUDA_TRY(cudaGetLastError());
