@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
 #include <utility>
 #include <vector>
@@ -143,6 +145,16 @@ struct bem_kernel_s {
 };
 
 namespace bem {
+// True on the first call for the current device (devices 0..63) with this flag:
+// one-time per-device setup such as kernel attributes, which are per device.
+// Concurrent first calls may both see true; the setup they guard is idempotent.
+inline bool first_on_device(std::atomic<unsigned long long>& seen) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  return (seen.fetch_or(bit) & bit) == 0;
+}
+
 void set_error(const std::string& msg);
 // number of kernel launches issued by the library (for launch accounting)
 void note_launches(long long n);

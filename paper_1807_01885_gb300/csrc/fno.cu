@@ -654,11 +654,8 @@ bool width_ok(int c) { return c == 1 || c == 7 || c == 8 || c == 16 || c == 32 |
 
 void wgrad(const float* dY, int cout, const float* X, int cin, float* gw, float* gb, float* part, size_t P, int B,
            cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_pw_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) cudaFuncSetAttribute(k_pw_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   dim3 grid((unsigned)((P + FT - 1) / FT), B);
   const size_t sm = (size_t)(cout + cin) * FT * sizeof(float);
   k_pw_wgrad<<<grid, FT, sm, s>>>(dY, X, part, cout, cin, P);

@@ -291,14 +291,13 @@ template <typename T>
 static void set_smem_attrs() {
   using C = cplx<T>;
   constexpr int TR = RowsPerBlock<T>::value;
-  static bool done = false;
-  if (done) return;
+  static std::atomic<unsigned long long> done{0};
+  if (!first_on_device(done)) return;
   const int max_row = 2 * TR * (1 << MAX_LOGN) * (int)sizeof(C);
   const int max_col = 4 * (1 << MAX_LOGN) * (int)sizeof(C);
   cudaFuncSetAttribute(k_row_fwd<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_row);
   cudaFuncSetAttribute(k_row_inv<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_row);
   cudaFuncSetAttribute(k_col<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_col);
-  done = true;
 }
 
 template <typename T>

@@ -213,11 +213,10 @@ template <typename T, int LOGN, int LOGR>
 struct RowLaunch {
   using C = cplx<T>;
   static void pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s, const int* skip) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    if (first_on_device(attr)) {
       cudaFuncSetAttribute(k_row_fwd_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_row_inv_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr = true;
     }
     constexpr int N = 1 << LOGN;
     using PR = Plan<LOGN, LOGR>;
@@ -237,11 +236,9 @@ template <typename T, int LOGN, int LOGR>
 struct ColLaunch {
   using C = cplx<T>;
   static void pass(const bem_kernel_s* k, const int* skip, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    if (first_on_device(attr))
       cudaFuncSetAttribute(k_col_r<T, LOGN + 1, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr = true;
-    }
     constexpr int N = 1 << LOGN;
     using PC = Plan<LOGN + 1, LOGR>;
     constexpr int cpb = cols_per_block<T, LOGN + 1, LOGR>();
