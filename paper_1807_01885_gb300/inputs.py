@@ -38,8 +38,9 @@ def rough_surface(N, delta, seed, hurst=0.7, rms_slope=0.1, rolloff_frac=1.0 / 8
     Power spectrum flat below the roll-off q_r = 2 pi / (L rolloff_frac), falling as
     q^{-2(1+H)} above it up to the Nyquist wave number pi/delta, zero above; random
     Gaussian amplitudes and uniform phases from ``numpy.random.default_rng(seed)``;
-    zero mean; scaled so the spectral rms slope equals ``rms_slope``.  Returned as
-    the indenter height f = max(z) - z >= 0 (summits at f = 0).
+    zero mean; scaled so that the rms of its central-difference slope equals
+    ``rms_slope``.  Returned as the indenter height f = max(z) - z >= 0 (summits at
+    f = 0).
     """
     rng = np.random.default_rng(seed)
     L = N * delta
