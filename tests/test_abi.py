@@ -52,3 +52,60 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(bem, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         bem.load(str(tmp_path / "libbem.so"))
+
+
+def declared_signatures():
+    """(return type, name, [parameter types]) of every prototype in include/bem.h."""
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\s*\b(bem_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src):
+        params = [] if m.group(3).strip() == "void" else [p.strip() for p in m.group(3).split(",")]
+        # drop the parameter name, keep the type (with its stars)
+        types = [re.sub(r"\s*\b[A-Za-z_][A-Za-z_0-9]*$", "", p).strip() for p in params]
+        out.append((m.group(1).strip(), m.group(2), types))
+    return out
+
+
+def _expected(ctype):
+    """ctypes the binding may use for a C type of the header: scalars exactly, data
+    pointers as c_void_p or a POINTER of the pointee, opaque handles as c_void_p."""
+    from paper_1807_01885_gb300 import bem
+    scalars = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "float": ctypes.c_float,
+               "double": ctypes.c_double, "bem_status": ctypes.c_int32, "const char*": ctypes.c_char_p}
+    structs = {"bem_kernel_desc": bem.KernelDesc, "bem_problem": bem.Problem, "bem_result": bem.Result,
+               "bem_fno_desc": getattr(bem, "FnoDesc", None)}
+    t = " ".join(ctype.replace("*", " * ").split())
+    t = t.replace(" *", "*")
+    if t in scalars:
+        return {scalars[t]}
+    if t in ("bem_kernel", "bem_fno"):
+        return {ctypes.c_void_p}
+    if "*" in t:
+        bare = re.sub(r"\bconst\b", "", t).replace(" ", "")
+        base, stars = bare.rstrip("*"), len(bare) - len(bare.rstrip("*"))
+        ok = {ctypes.c_void_p}
+        if stars == 1 and base in scalars:
+            ok.add(ctypes.POINTER(scalars[base]))
+        if stars == 1 and structs.get(base) is not None:
+            ok.add(ctypes.POINTER(structs[base]))
+        if (stars == 1 and base in ("bem_kernel", "bem_fno")) or bare == "void**":
+            ok.add(ctypes.POINTER(ctypes.c_void_p))
+        return ok
+    raise AssertionError(f"unmapped C type {ctype!r}")
+
+
+def test_binding_signatures_match_header(bemlib):
+    """Every prototype's arity, argument types and return type agree with the ctypes
+    declarations of the binding: a drifted signature would pass arguments wrongly
+    without any error at the call."""
+    sigs = declared_signatures()
+    assert sorted(n for _, n, _ in sigs) == declared_entry_points()
+    for ret, name, params in sigs:
+        fn = getattr(bemlib, name)
+        assert fn.argtypes is not None, f"{name}: argtypes not set"
+        assert len(fn.argtypes) == len(params), (name, params, fn.argtypes)
+        for i, (c, py) in enumerate(zip(params, fn.argtypes)):
+            assert py in _expected(c), f"{name} argument {i}: header {c!r}, binding {py}"
+        assert fn.restype in _expected(ret), f"{name} return: header {ret!r}, binding {fn.restype}"
