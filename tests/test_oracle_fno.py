@@ -67,3 +67,12 @@ def test_gradients_by_finite_differences():
             fd = (lp - lm) / (2 * eps)
             an = G[key].reshape(-1)[i]
             assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (key, i, an, fd)
+
+
+def test_gelu_is_z_times_normal_cdf():
+    """gelu(z) = z Phi(z), Phi the standard normal distribution function (scipy's).
+    The oracle's 1 + erf form cancels in the far negative tail, so the bound there is
+    absolute (1e-15, against values of order 1e-9 at z = -6)."""
+    stats = pytest.importorskip("scipy.stats")
+    z = np.linspace(-6, 6, 49)
+    np.testing.assert_allclose(fno.gelu(z), z * stats.norm.cdf(z), rtol=1e-14, atol=1e-15)
