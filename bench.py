@@ -15,7 +15,9 @@ time is the time to converge.  Extra keys: matvec-only throughput on 8 distinct
 inputs (larger than L2), the roofline of the dominant pass, the end-to-end number
 through the C ABI with host buffers, the CPU oracle timed on a bounded sample, the
 256-instance batch of uneven grids (batched vs one after another), the adhesive
-ramp (200 displacement steps at N = 512) and the learned warm start.
+ramp (200 displacement steps at N = 512) and the learned warm start.  A comparison
+line times the same products through torch.fft (cuFFT R2C, pointwise K^, C2R); it
+is never part of the library's path.
 
 --impl reference times the CPU FP64 oracle (the method written plainly, see
 oracle/) on the same workload: each step is one N = 2048 operator product.
@@ -101,6 +103,45 @@ def alg_bytes(N, elem=4):
     col = 2 * c * N * (N + 1) + elem * (N + 1) ** 2
     row_inv = c * N * (N + 1) + elem * N * N
     return row_fwd, col, row_inv
+
+
+def library_fft_khat(torch, table, N, dtype):
+    """K^ on the half grid M x (N+1) of a length-M real FFT along rows (M = 2N), from
+    the folded (N+1) x (N+1) table the library exports: period row i is table row
+    min(i, M - i).  For the comparison line only."""
+    return torch.cat([table, table[1:N].flip(0)], 0).to(dtype).contiguous()
+
+
+def library_fft_matvec(torch, khat_half, p, pad):
+    """u = K p by the vendor FFT behind torch.fft (cuFFT on a GPU): copy p into the
+    zero-padded M x M buffer ``pad`` (zero outside the window), R2C, multiply by K^,
+    C2R with the 1/M^2 normalisation, crop.  The comparison line of the benchmark,
+    never the product path."""
+    N = p.shape[0]
+    pad[:N, :N].copy_(p)
+    U = torch.fft.irfft2(torch.fft.rfft2(pad) * khat_half, s=tuple(pad.shape))
+    return U[:N, :N]
+
+
+def library_fft_bench(torch, k, P, U, stream, reps=100):
+    """Products per second of the torch.fft comparison on the inputs of the
+    matvec-only loop, and its relative L2 difference from the library's product."""
+    N = P[0].shape[0]
+    kh = library_fft_khat(torch, k.table(device=P[0].device), N, torch.float32)
+    pad = torch.zeros((2 * N, 2 * N), dtype=torch.float32, device=P[0].device)
+    out = [library_fft_matvec(torch, kh, x, pad).clone() for x in P]
+    rel = max(float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
+              for a, b in zip(out, U))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(reps):
+        library_fft_matvec(torch, kh, P[j % len(P)], pad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"impl": "torch.fft rfft2 x K^ x irfft2 (cuFFT), FP32, zero-padded 2N x 2N",
+            "value": 1000.0 / ms, "unit": UNIT, "ms_per_matvec": ms, "rel_l2_vs_library": rel}
 
 
 class Clocks:
@@ -526,6 +567,11 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     mv_ms = e0.elapsed_time(e1) / reps
+    # comparison only: the same products through torch.fft (cuFFT) on the same inputs
+    try:
+        lib_fft = library_fft_bench(torch, k0, P, U, stream)
+    except Exception as exc:                    # a comparison line never fails the bench
+        lib_fft = {"error": f"{type(exc).__name__}: {exc}"}
 
     # dominant pass: mean duration over its launches inside the timed region (CUDA
     # events recorded by the library on the launching stream around every pass)
@@ -571,6 +617,7 @@ def run_ours(args):
         "matvecs_per_solve": mv / args.steps,
         "matvec_only": {"value": 1000.0 / mv_ms, "unit": UNIT, "ms_per_matvec": mv_ms,
                         "alg_bytes": sum(rb), "gbs": sum(rb) / (mv_ms * 1e-3) / 1e9},
+        "library_fft_comparison": lib_fft,
         "passes_ms_mean": dict(zip(names, pass_mean)),
         "passes_timing_region": "a second run of the same steps with CUDA events around every pass",
         "passes_launches": dict(zip(names, pass_n)),

@@ -200,3 +200,26 @@ def test_peaks_read_measured_file(bench):
         assert kind == "measured" and hbm > 1000
     else:
         assert (hbm, kind) == (6800.0, "fallback")
+
+
+def test_library_fft_comparison_matches_oracle_operator(bench):
+    """The benchmark's torch.fft comparison line computes the same operator as the
+    oracle's Eq. (11) product: the half-grid K^ unfolded from an (N+1)^2 table equals
+    the oracle's padded grid, and the product agrees on a ragged rough pressure field."""
+    import torch
+    from oracle import operator as oop
+    N, delta = 24, 1.0 / 24
+    Kg = oop.khat_grid(N, delta, 0.1, 3.0, 0.3, 1.0, 0.45)
+    table = torch.tensor(Kg[:N + 1, :N + 1])
+    kh = bench.library_fft_khat(torch, table, N, torch.float64)
+    assert kh.shape == (2 * N, N + 1)
+    np.testing.assert_array_equal(kh.numpy(), Kg[:, :N + 1])
+    rng = np.random.default_rng(4)
+    p = np.maximum(rng.standard_normal((N, N)), 0.0)
+    pad = torch.zeros((2 * N, 2 * N), dtype=torch.float64)
+    u = bench.library_fft_matvec(torch, kh, torch.tensor(p), pad).numpy()
+    ref = oop.matvec_dense(Kg, p)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-13
+    # the buffer outside the window stays zero, so a second call gives the same product
+    u2 = bench.library_fft_matvec(torch, kh, torch.tensor(p), pad).numpy()
+    np.testing.assert_array_equal(u, u2)
