@@ -438,16 +438,55 @@ def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
             "all_converged": all(r["status"] == 0 for r in r_cold + r_warm)}
 
 
+_ORACLE_CASE = {}
+
+
+def _oracle_case(N=N_GRID):
+    """The oracle's padded K^ grid of the first timed instance and a pressure field."""
+    if N not in _ORACLE_CASE:
+        from oracle import operator
+        from paper_1807_01885_gb300 import inputs
+        inst = inputs.batch_instance(SEED0, sizes=(N,))
+        Kg = operator.khat_grid(N, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"])
+        _ORACLE_CASE[N] = (Kg, np.random.default_rng(0).random((N, N)))
+    return _ORACLE_CASE[N]
+
+
 def cpu_oracle_matvecs(seconds_hint=True):
     """One N = 2048 product of the FP64 oracle (its own radix-2 FFT), timed."""
     from oracle import operator
-    from paper_1807_01885_gb300 import inputs
-    inst = inputs.batch_instance(SEED0, sizes=(N_GRID,))
-    Kg = operator.khat_grid(N_GRID, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"])
-    p = np.random.default_rng(0).random((N_GRID, N_GRID))
+    Kg, p = _oracle_case()
     t0 = time.perf_counter()
     operator.matvec_fft(Kg, p)
     return time.perf_counter() - t0
+
+
+def cpu_library_fft(reps=4, N=N_GRID):
+    """The same FP64 product through scipy's FFT (pocketfft) on every host core: the
+    'reasonable CPU' comparison next to the one-thread oracle.  Returns a JSON dict."""
+    import scipy.fft as sfft
+    from oracle import operator
+    Kg, p = _oracle_case(N)
+    M = 2 * N
+    kh = np.ascontiguousarray(Kg[:, :N + 1])
+    pad = np.zeros((M, M))
+    cores = os.cpu_count() or 1
+
+    def product():
+        pad[:N, :N] = p
+        return sfft.irfft2(sfft.rfft2(pad, workers=cores) * kh, s=(M, M), workers=cores)[:N, :N]
+
+    u = product()
+    ref = operator.matvec_fft(Kg, p) if N <= 256 else None
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        product()
+    dt = (time.perf_counter() - t0) / reps
+    out = {"kind": "library FFT (scipy.fft pocketfft, FP64), not the oracle", "value": 1.0 / dt, "unit": UNIT,
+           "cores": cores, "sample": f"{reps} FP64 products at N={N} after 1 untimed"}
+    if ref is not None:
+        out["rel_l2_vs_oracle"] = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    return out
 
 
 REF_MAX_TIMED = 6
@@ -641,6 +680,10 @@ def run_ours(args):
         dt = cpu_oracle_matvecs()
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"1 FP64 product at N={N_GRID} (oracle radix-2 FFT, numpy, one thread)"}
+        try:
+            line["cpu_library_fft"] = cpu_library_fft()
+        except Exception as exc:                # a comparison line never fails the bench
+            line["cpu_library_fft"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in insts:

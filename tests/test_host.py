@@ -223,3 +223,11 @@ def test_library_fft_comparison_matches_oracle_operator(bench):
     # the buffer outside the window stays zero, so a second call gives the same product
     u2 = bench.library_fft_matvec(torch, kh, torch.tensor(p), pad).numpy()
     np.testing.assert_array_equal(u, u2)
+
+
+def test_cpu_library_fft_line_matches_oracle(bench):
+    """The multi-core scipy FFT comparison computes the oracle's product (N = 64)."""
+    pytest.importorskip("scipy.fft")
+    out = bench.cpu_library_fft(reps=1, N=64)
+    assert out["rel_l2_vs_oracle"] < 1e-13
+    assert out["value"] > 0 and out["cores"] >= 1
