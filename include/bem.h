@@ -214,8 +214,16 @@ typedef struct {
   int32_t width, modes, layers, hidden;
 } bem_fno_desc;
 typedef struct bem_fno_s* bem_fno;
+/* Creates a network on the current device with every parameter zero (load them
+ * with bem_fno_set_params); the handle owns its parameter, optimiser and activation
+ * buffers (activations grow with B and N on demand).  BEM_EINVAL for a NULL
+ * argument, a width or hidden size outside the list above, modes < 1 or layers
+ * outside [1, 16]; BEM_ENOMEM (or BEM_ECUDA) if an allocation fails; *out is NULL on
+ * failure. */
 bem_status bem_fno_create(const bem_fno_desc* desc, bem_fno* out);
+/* Synchronises the device and frees everything the handle owns; NULL is a no-op. */
 bem_status bem_fno_destroy(bem_fno f);
+/* Length of the parameter vector (floats), -1 for a NULL handle. */
 int64_t bem_fno_param_count(bem_fno f);
 /* copy in float parameters (host or device); resets the optimiser state */
 bem_status bem_fno_set_params(bem_fno f, const float* params, int64_t count, void* cuda_stream);
@@ -226,6 +234,8 @@ bem_status bem_fno_get_params(bem_fno f, float* params, int64_t count, int32_t r
  * log(E1/E2)/log 20, nu1, nu2, (column + 1/2)/N, (row + 1/2)/N.  B <= 4096. */
 bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* heights, const double* params, float* x,
                             void* cuda_stream);
+/* out = network(x) for B samples (device arrays x [B][7][N][N], out [B][N][N]);
+ * asynchronous on cuda_stream.  BEM_EINVAL for host arrays, B < 1 or N < 2 modes. */
 bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, float* out, void* cuda_stream);
 /* forward + backward of the loss mean((out - target)^2); writes the gradient (host or
  * device, may be NULL) and the loss; synchronises the stream */

@@ -891,7 +891,7 @@ bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, floa
   }
   if (!is_dev(x) || !is_dev(out)) { set_error("FNO arrays must be device arrays"); return BEM_EINVAL; }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  bem_status st = ensure(f, B, N, false || (f->cap_train && B <= f->capB && N <= f->capN), s);
+  bem_status st = ensure(f, B, N, f->cap_train && B <= f->capB && N <= f->capN, s);
   if (st != BEM_OK) return st;
   st = forward(f, B, N, x, f->cap_train, s);
   if (st != BEM_OK) return st;
