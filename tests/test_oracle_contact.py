@@ -138,3 +138,68 @@ def test_sigma_c_constant_from_paper():
     E1, nu1, dg, delta = 2.0, 0.3, 0.01, 0.05
     s = contact.sigma_c(E1, nu1, dg, delta)
     assert s * s * c * delta == pytest.approx(E1 / (1 - nu1 ** 2) * dg, rel=1e-14)
+
+
+def test_pk_matches_active_set_enumeration():
+    """Brute force on a 4 x 4 window: of the 65536 candidate contact sets S, exactly one
+    gives p_S = K_SS^{-1} (d - f)_S >= 0 with no penetration outside S (the QP's
+    unique solution, K being positive definite); the CG returns that pressure."""
+    import itertools
+    N, delta = 4, 0.15
+    Kg, mv = _mv(N, delta, 0.3, 2.0, 0.3, 1.0, 0.4)
+    Km = operator.dense_matrix(Kg)
+    rng = np.random.default_rng(8)
+    f = inputs.sphere_height(N, delta, 0.4) + 0.004 * rng.standard_normal((N, N))
+    f -= f.min()
+    d = 0.03
+    b = (d - f).reshape(-1)
+    found = []
+    for mask in itertools.product([False, True], repeat=N * N):
+        S = np.array(mask)
+        p = np.zeros(N * N)
+        if S.any():
+            p[S] = np.linalg.solve(Km[np.ix_(S, S)], b[S])
+        g = Km @ p - b
+        if p.min() >= -1e-12 * max(p.max(), 1e-300) and g[~S].min(initial=0.0) >= -1e-12 * np.abs(b).max():
+            found.append((S, p))
+    assert len(found) == 1
+    S_ref, p_ref = found[0]
+    assert 0 < S_ref.sum() < N * N                     # a partial contact, not a trivial case
+    s = contact.solve_nonadhesive(mv, f, delta, "depth", d, tol=1e-14)
+    np.testing.assert_allclose(s["p"].reshape(-1), p_ref, atol=1e-10 * p_ref.max())
+
+
+def test_adhesive_steps_are_fixed_points_of_the_rules():
+    """Every step of an oracle pull-off ramp (N = 16, homogeneous) satisfies the rules
+    of the Sec. 2 procedure, checked with the dense matrix of Eq. (1): on C the
+    displacement is exactly d - f (dense solve of K_CC p_C = (d - f)_C), p = 0 off C,
+    no cell off C penetrates, and no boundary cell of C carries a tension above
+    sigma_c (Eq. 12).  The ramp must reach tension and detach cells, so the rules
+    that matter in adhesion are exercised."""
+    N, R, E, nu = 16, 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Kg, mv = _mv(N, delta, np.inf, E, nu, E, nu)
+    Km = operator.dense_matrix(Kg)
+    Es = kernel.e_star(E, nu)
+    dg = (2 * delta) ** 3 * 8 * Es / (np.pi * R * R)
+    sc = contact.sigma_c(E, nu, dg, delta)
+    f = inputs.sphere_height(N, delta, R)
+    d_max = (3.5 * delta) ** 2 / R
+    depths = np.concatenate([np.linspace(0, d_max, 4), np.linspace(d_max, -d_max, 16)[1:]])
+    out = contact.adhesive_ramp(mv, f, delta, depths, sc, tol=1e-13)
+    saw_tension = False
+    for o in out:
+        C, p, d = o["C"].reshape(-1), o["p"].reshape(-1), o["d"]
+        b = (d - f).reshape(-1)
+        assert np.all(p[~C] == 0.0)
+        if C.any():
+            pc = np.linalg.solve(Km[np.ix_(C, C)], b[C])
+            np.testing.assert_allclose(p[C], pc, atol=1e-9 * np.abs(pc).max())
+        g = Km @ p - b
+        assert g[~C].min(initial=0.0) >= -1e-10 * max(np.abs(b).max(), 1e-300)
+        B = contact.boundary_cells(o["C"]).reshape(-1)
+        assert np.all(-p[B] <= sc)
+        saw_tension |= bool((p < 0).any())
+    assert saw_tension
+    n = [o["n_contact"] for o in out]
+    assert max(n) > 0 and n[-1] < max(n)
