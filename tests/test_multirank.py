@@ -37,7 +37,9 @@ def _rank(rank, world, port, out):
 def test_aggregation_over_two_gloo_ranks():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    # the manager process is spawned too: forking a process that already runs threads
+    # (BLAS, FFT workers of earlier tests) can deadlock the child
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn")
         res = dict(out)
