@@ -144,6 +144,54 @@ def library_fft_bench(torch, k, P, U, stream, reps=100):
             "value": 1000.0 / ms, "unit": UNIT, "ms_per_matvec": ms, "rel_l2_vs_library": rel}
 
 
+def fft_nominal_flops(N):
+    """Nominal flops of one product (5 M log2 M per complex length-M transform, a real
+    one counted as half): two row passes of N real transforms, and N + 1 columns of a
+    forward and an inverse complex transform, M = 2N."""
+    M = 2 * N
+    c = 5.0 * M * np.log2(M)
+    return 2 * N * (c / 2) + (N + 1) * 2 * c
+
+
+def fp64_bench(torch, bem, inst, stream, reps=20):
+    """The FP64 product at N = 2048 against a cuBLAS DGEMM timed in the same run: the
+    double path is bound by the FP64 pipe, so its roofline is a flop rate."""
+    N = inst["N"]
+    k = bem.Kernel(N, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"], precision="fp64")
+    try:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        P = [torch.rand((N, N), dtype=torch.float64, device=dev) for _ in range(2)]
+        U = [torch.empty_like(x) for x in P]
+        for j in range(2):
+            k.matvec(P[j], U[j])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(reps):
+            k.matvec(P[j % 2], U[j % 2])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    finally:
+        k.close()
+    n = 4096
+    A = torch.randn((n, n), dtype=torch.float64, device=dev)
+    B = torch.randn((n, n), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(A, B)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        torch.matmul(A, B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gemm = 2.0 * n ** 3 / (e0.elapsed_time(e1) / 10 * 1e-3) / 1e12
+    tf = fft_nominal_flops(N) / (ms * 1e-3) / 1e12
+    return {"ms_per_matvec": ms, "nominal_gflop": fft_nominal_flops(N) / 1e9, "tflops": tf,
+            "dgemm_tflops_measured": gemm, "frac_of_dgemm": tf / gemm,
+            "note": "FP64 product (nominal transform flops) against cuBLAS DGEMM 4096^3 in the same run"}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -611,6 +659,10 @@ def run_ours(args):
         lib_fft = library_fft_bench(torch, k0, P, U, stream)
     except Exception as exc:                    # a comparison line never fails the bench
         lib_fft = {"error": f"{type(exc).__name__}: {exc}"}
+    try:
+        fp64 = fp64_bench(torch, bem, insts[0]["inst"], stream)
+    except Exception as exc:
+        fp64 = {"error": f"{type(exc).__name__}: {exc}"}
 
     # dominant pass: mean duration over its launches inside the timed region (CUDA
     # events recorded by the library on the launching stream around every pass)
@@ -657,6 +709,7 @@ def run_ours(args):
         "matvec_only": {"value": 1000.0 / mv_ms, "unit": UNIT, "ms_per_matvec": mv_ms,
                         "alg_bytes": sum(rb), "gbs": sum(rb) / (mv_ms * 1e-3) / 1e9},
         "library_fft_comparison": lib_fft,
+        "fp64_product": fp64,
         "passes_ms_mean": dict(zip(names, pass_mean)),
         "passes_timing_region": "a second run of the same steps with CUDA events around every pass",
         "passes_launches": dict(zip(names, pass_n)),
