@@ -231,3 +231,13 @@ def test_cpu_library_fft_line_matches_oracle(bench):
     out = bench.cpu_library_fft(reps=1, N=64)
     assert out["rel_l2_vs_oracle"] < 1e-13
     assert out["value"] > 0 and out["cores"] >= 1
+
+
+def test_fft_nominal_flops(bench):
+    """5 M log2 M per complex transform of length M = 2N, a real transform as half:
+    1.51 GFLOP per product at N = 2048, four times as much per doubling of N (plus
+    the log factor)."""
+    assert bench.fft_nominal_flops(2048) == pytest.approx(1.51044096e9, rel=1e-12)
+    M = 16
+    c = 5 * M * 4
+    assert bench.fft_nominal_flops(8) == 2 * 8 * c / 2 + 9 * 2 * c
