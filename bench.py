@@ -500,7 +500,7 @@ def _oracle_case(N=N_GRID):
     return _ORACLE_CASE[N]
 
 
-def cpu_oracle_matvecs(seconds_hint=True):
+def cpu_oracle_matvecs():
     """One N = 2048 product of the FP64 oracle (its own radix-2 FFT), timed."""
     from oracle import operator
     Kg, p = _oracle_case()

@@ -8,7 +8,6 @@ repeat the same trajectory (same inputs, same device-side arithmetic).
 import numpy as np
 import torch
 
-from . import bem
 
 
 def depth_schedule(d_max, d_min, n_load, n_unload):
