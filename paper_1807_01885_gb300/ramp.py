@@ -9,7 +9,6 @@ import numpy as np
 import torch
 
 
-
 def depth_schedule(d_max, d_min, n_load, n_unload):
     """Depths of a loading phase 0 -> d_max and a pull-off phase d_max -> d_min."""
     return np.concatenate([np.linspace(0.0, d_max, n_load), np.linspace(d_max, d_min, n_unload + 1)[1:]])
