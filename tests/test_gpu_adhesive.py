@@ -128,3 +128,40 @@ def test_ramp_resume_repeats_trajectory(cuda, tmp_path):
     assert [r["n_contact"] for r in part + resumed] == [r["n_contact"] for r in full]
     for a, b in zip(part + resumed, full):
         assert a["force"] == b["force"]
+
+
+def test_force_controlled_pull_off_jkr(cuda):
+    """Force control (the variant beside the displacement control of Sec. 2): E1 = E2,
+    jump-off radius 16 cells.  Loaded by depth, then released target by target; every
+    target is met by the library's depth-controlled adhesive steps to the search
+    tolerance, the indenter jumps off at the first target below the force minimum of
+    the same branch followed in small depth steps, and that force is the JKR pull-off
+    force -(3/2) pi R dgamma (Eqs. 22/23 at epsilon = 0) within 6 %."""
+    N, R, E, nu = 256, 1.0, 1.0, 0.3
+    delta = 1.0 / N
+    Es = okernel.e_star(E, nu)
+    a_d = 16 * delta
+    dg = a_d ** 3 * 8 * Es / (np.pi * R * R)
+    a_F = 9 ** (1 / 3) * a_d
+    f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda)
+    d_max = (1.3 * a_F) ** 2 / R
+    d_end = 1.2 * analytic.jkr_jump_off(R, Es, dg)[2]
+    Fj = analytic.jkr_pull_off_force(R, dg)
+    spacing = 0.02 * abs(Fj)
+    rtol = 2e-3
+    with bem.Kernel(N, delta, np.inf, E, nu, E, nu) as k:
+        load, (p, mask) = ramp.run(k, f, np.linspace(0.0, d_max, 10), dg, tol=1e-10, with_state=True)
+        F0 = load[-1]["force"]
+        targets = np.concatenate([np.linspace(F0, 0.8 * Fj, 8)[1:], 0.8 * Fj - spacing * np.arange(1, 26)])
+        rec, jumped = ramp.force_run(k, f, targets, dg, d_max, p, mask, F0, 2 * load[-1]["a_eq"] * Es, tol=1e-10,
+                                     rtol=rtol, max_step=(d_max - d_end) / 90)
+        disp = ramp.run(k, f, np.linspace(d_max, d_end, 91), dg, tol=1e-10, state=(1, p, mask))
+    assert all(r["status"] == 0 for r in load + disp)
+    assert jumped and 0 < len(rec) < len(targets)
+    for r in rec:
+        assert abs(r["force"] - r["target"]) <= rtol * max(abs(r["target"]), F0) * (1 + 1e-9)
+    assert all(b["d"] < a["d"] for a, b in zip(rec, rec[1:]))
+    F_min = min(r["force"] for r in disp)
+    F_last = rec[-1]["force"]
+    assert F_min - 0.03 * abs(Fj) <= F_last < F_min + spacing + 0.03 * abs(Fj)
+    assert F_last / Fj == pytest.approx(1.0, abs=0.06)

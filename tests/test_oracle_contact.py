@@ -203,3 +203,51 @@ def test_adhesive_steps_are_fixed_points_of_the_rules():
     assert saw_tension
     n = [o["n_contact"] for o in out]
     assert max(n) > 0 and n[-1] < max(n)
+
+
+def test_force_controlled_pull_off_on_oracle_steps():
+    """The force-controlled pull-off search (host logic of the package) driven by the
+    oracle's displacement-controlled adhesive steps, homogeneous JKR case (N = 64,
+    jump-off radius 5 cells): every reached target is met to the search tolerance, the
+    indenter jumps off at the first target below the force minimum of the branch
+    followed in small depth steps (to within the few cells by which the two depth
+    sequences detach differently), and that minimum is the JKR pull-off force
+    -(3/2) pi R dgamma within the discretisation error of this grid (15 %)."""
+    from paper_1807_01885_gb300 import ramp
+    N, R, E, nu = 64, 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Es = kernel.e_star(E, nu)
+    a_d = 5 * delta
+    dg = a_d ** 3 * 8 * Es / (np.pi * R * R)
+    a_F = 9 ** (1 / 3) * a_d
+    _, mv = _mv(N, delta, np.inf, E, nu, E, nu)
+    f = inputs.sphere_height(N, delta, R)
+    sc = contact.sigma_c(E, nu, dg, delta)
+    d_max = (1.4 * a_F) ** 2 / R
+    d_end = 1.3 * analytic.jkr_jump_off(R, Es, dg)[2]
+    last = contact.adhesive_ramp(mv, f, delta, np.linspace(0, d_max, 6), sc, tol=1e-10)[-1]
+    Fj = analytic.jkr_pull_off_force(R, dg)
+
+    def solve_depth(d, state):
+        p, C = state
+        p2, C2, _, _ = contact.adhesive_step(mv, f, d, C, sc, p_prev=p, tol=1e-10)
+        return (p2, C2), float(delta * delta * p2.sum()), int(C2.sum())
+
+    spacing = 0.05 * abs(Fj)
+    targets = np.concatenate([np.linspace(last["force"], 0.7 * Fj, 6)[1:],
+                              0.7 * Fj - spacing * np.arange(1, 15)])
+    step = (d_max - d_end) / 60
+    rec, jumped = ramp.force_pull_off(solve_depth, targets, d_max, (last["p"], last["C"]), last["force"],
+                                      2 * last["a_eq"] * Es, rtol=2e-3, max_step=step)
+    assert jumped and 0 < len(rec) < len(targets)
+    for r in rec:
+        assert abs(r["force"] - r["target"]) <= 2e-3 * max(abs(r["target"]), last["force"]) + 1e-15
+    assert all(b["d"] < a["d"] for a, b in zip(rec, rec[1:]))
+    disp = contact.adhesive_ramp(mv, f, delta, np.linspace(d_max, d_end, 61)[1:], sc, C0=last["C"], tol=1e-10)
+    F_min = min(o["force"] for o in disp)
+    F_last = rec[-1]["force"]
+    # the last reached target is above the branch minimum, the next one below it; the
+    # two depth sequences differ, so the cells detach in a slightly different order
+    # (3 % of the pull-off force allowed for that)
+    assert F_min - 0.03 * abs(Fj) <= F_last < F_min + spacing + 0.03 * abs(Fj)
+    assert F_last / Fj == pytest.approx(1.0, abs=0.15)
