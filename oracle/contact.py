@@ -7,8 +7,9 @@ sampled kernel).
 Conventions (Sec. 2, condition (c)): p > 0 is compressive, tension is p < 0; u is the
 surface displacement into the body; f is the indenter height above its lowest
 point; d is the indentation depth; the gap is g = u + f - d.  Non-adhesive contact
-(Sec. 2, "inverse problem ... conjugate gradient method as described in [8]") means
-p >= 0, g >= 0, p g = 0; the total force is F = delta^2 sum p.
+(Sec. 2: the pressures for a prescribed surface displacement, found by the
+conjugate-gradient method of the paper's reference [8]) means p >= 0, g >= 0,
+p g = 0; the total force is F = delta^2 sum p.
 
 * ``solve_nonadhesive``  Polonsky-Keer constrained conjugate gradients, the method
   the paper cites as [8], under depth control (d given) or load control (F given,
@@ -16,15 +17,17 @@ p >= 0, g >= 0, p g = 0; the total force is F = delta^2 sum p.
 * ``kkt_violation``      complementarity check of a computed solution.
 * ``sigma_c``            Eq. (12), the mesh-dependent detachment stress.
 * ``boundary_cells``     cells of a contact set with a 4-neighbour outside it (the
-  window edge counts as outside) - the "elements at the boundary" of Sec. 2.
+  window edge counts as outside): the cells on the rim of the contact area to
+  which Sec. 2 applies the detachment test.
 * ``solve_fixed_set``    the inverse problem on a fixed contact area, p free in sign.
 * ``adhesive_step``      one displacement-controlled step of Sec. 2's adhesive
   procedure: solve on the fixed area, add penetrating cells, detach boundary cells
   whose tension exceeds sigma_c (all at once), repeat until the area is unchanged.
 * ``adhesive_ramp``      a sequence of such steps over a list of depths.
 
-Parity status: pinned by tests (KKT, NNLS brute force, Hertz, flat punch, thin
-layer, JKR, Eq. 16) - see tests/test_oracle_contact.py.
+Parity status: pinned by tests (KKT, enumeration of every contact set of a tiny
+window, NNLS, Hertz, flat punch, thin layer, JKR, Eq. 16, fixed points of the
+adhesive rules) - see tests/test_oracle_contact.py.
 """
 import numpy as np
 
