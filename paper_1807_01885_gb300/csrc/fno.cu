@@ -819,11 +819,16 @@ bem_status bem_fno_create(const bem_fno_desc* desc, bem_fno* out) {
     delete f;
     return cuda_fail(e, "cudaMalloc(fno parameters)");
   }
-  cudaMemset(f->w, 0, f->P * sizeof(float));
-  cudaMemset(f->wb, 0, f->P * sizeof(bf16));
-  cudaMemset(f->g, 0, f->P * sizeof(float));
-  cudaMemset(f->m1, 0, f->P * sizeof(float));
-  cudaMemset(f->m2, 0, f->P * sizeof(float));
+  e = cudaMemset(f->w, 0, f->P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(f->wb, 0, f->P * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMemset(f->g, 0, f->P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(f->m1, 0, f->P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(f->m2, 0, f->P * sizeof(float));
+  if (e != cudaSuccess) {
+    for (void* p : f->owned) cudaFree(p);
+    delete f;
+    return cuda_fail(e, "cudaMemset(fno parameters)");
+  }
   *out = f;
   return BEM_OK;
 }
