@@ -128,7 +128,10 @@ bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream);
  * Non-adhesive: Polonsky-Keer constrained conjugate gradients (the method the
  * paper cites for the inverse problem, Sec. 2).  Adhesive: Sec. 2's procedure at
  * one depth: CG on the fixed contact area, penetrating cells join, boundary cells
- * with tension above sigma_c (Eq. 12, compared in double) detach, repeat. */
+ * with tension above sigma_c (Eq. 12, compared in double) detach, repeat.
+ * Diagnostics: with the environment variable BEM_TRACE set (any value) when the
+ * process makes its first non-adhesive solve, every 8-iteration chunk prints the
+ * iteration count, the residual and the contact-set counts to stderr. */
 bem_status bem_solve_contact(bem_kernel k, const bem_problem* prob, void* p_out,
                              bem_result* res, void* cuda_stream);
 

@@ -346,12 +346,9 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
   k->prec = desc->precision;
   k->elem = (k->prec == BEM_FP64) ? sizeof(double) : sizeof(float);
   cudaGetDevice(&k->dev);
-  {
-    const char* alt = getenv("BEM_COL_RADIX_ALT");
-    k->col_radix_alt = (alt != nullptr && alt[0] == '1') ? 1 : 0;
-    const char* ralt = getenv("BEM_ROW_RADIX_ALT");
-    k->row_radix_alt = (ralt != nullptr && ralt[0] == '1') ? 1 : 0;
-  }
+  // radix 16 for every float pass until bem_set_radix or bem_autotune says otherwise
+  k->col_radix_alt = 0;
+  k->row_radix_alt = 0;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t n = (size_t)k->N * k->N;
   Workspace& w = k->ws;

@@ -118,8 +118,8 @@ struct bem_kernel_s {
   int prec;       // BEM_FP64 / BEM_FP32
   size_t elem;    // sizeof(real)
   int dev;
-  int col_radix_alt;   // 1: radix 8 for the float column pass (bem_set_radix, bem_autotune, BEM_COL_RADIX_ALT)
-  int row_radix_alt;   // 1: radix 8 for the float row passes (bem_set_radix, bem_autotune, BEM_ROW_RADIX_ALT)
+  int col_radix_alt;   // 1: radix 8 for the float column pass (bem_set_radix, bem_autotune)
+  int row_radix_alt;   // 1: radix 8 for the float row passes (bem_set_radix, bem_autotune)
   bem::Workspace ws;
   // per-pass CUDA-event timing (bem_set_pass_timing): pending (start, end) pairs,
   // harvested into totals at synchronisation points
