@@ -241,3 +241,38 @@ def test_fft_nominal_flops(bench):
     M = 16
     c = 5 * M * 4
     assert bench.fft_nominal_flops(8) == 2 * 8 * c / 2 + 9 * 2 * c
+
+
+def test_reference_arm_line_contract(bench, monkeypatch, capsys):
+    """`bench.py --impl reference` prints one JSON line with the keys the benchmark
+    contract needs; the oracle product is replaced by a fixed 0.5 s stand-in so the
+    line's arithmetic can be checked (a bounded sample: at most 6 timed products)."""
+    import json
+    monkeypatch.setattr(bench, "cpu_oracle_matvecs", lambda: 0.5)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "40", "--warmup", "3"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_reference(bench.parse())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] == pytest.approx(2.0) and d["ms_per_step"] == pytest.approx(500.0)
+    assert d["higher_is_better"] is True and d["steps"] == 40 and d["warmup"] == 3
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "6 timed" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_nothing(bench, monkeypatch, capsys):
+    """Under a multi-process launch only rank 0 runs and prints the reference arm."""
+    calls = []
+    monkeypatch.setattr(bench, "cpu_oracle_matvecs", lambda: calls.append(1) or 0.5)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.run_reference(bench.parse())
+    assert capsys.readouterr().out.strip() == "" and not calls
