@@ -1,13 +1,15 @@
 """Builds libbem.so in-tree from csrc/*.cu for sm_103a (nvcc, no cmake).
 
 Usage: python -m paper_1807_01885_gb300.build [--force]
-Objects go to paper_1807_01885_gb300/_build/, the library to
+Objects go to paper_1807_01885_gb300/_build/<machine>/ (one folder per host
+architecture, so x86-64 and aarch64 objects never mix), the library to
 paper_1807_01885_gb300/libbem.so.  Translation units compile in parallel; a unit is
 rebuilt when it or any header under csrc/ or include/ is newer than its object.
 """
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -16,7 +18,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+BUILD = os.path.join(PKG, "_build", platform.machine() or "host")
 LIB = os.path.join(PKG, "libbem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
