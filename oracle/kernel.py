@@ -169,3 +169,33 @@ def khat_transfer_matrix(k, h, E1, nu1, E2, nu2):
     c = np.linalg.solve(S0[2:4, :], rhs)
     uz0 = (S0 @ c)[1]
     return float(uz0.real)
+
+
+def khat_multilayer(k, layers, E_sub, nu_sub):
+    """Surface compliance u_z(0)/p0 of a stack of bonded layers on a substrate, by the
+    same transfer-matrix solve of Eq. (5) as ``khat_transfer_matrix`` (the multi-layer
+    generalisation of Eqs. 9/10, which the paper gives for one layer).
+
+    ``layers`` lists (thickness, E, nu) from the surface down.  At the bottom of the
+    stack the state lies in the decaying invariant subspace of the substrate's system
+    matrix (finite E_sub), or has zero displacements (E_sub = inf: a rigid base, the
+    tractions free); every layer carries the state from its bottom to its top by
+    expm(-A h), which keeps displacements and tractions continuous at each interface
+    (condition (a) at every interface); at z = 0 s_kz = 0 and s_zz = -1 (conditions
+    (b), (c)).  Scalar k > 0; moderate k times the total thickness.
+    """
+    if np.isinf(E_sub):
+        Q = np.zeros((4, 2), dtype=np.complex128)
+        Q[2, 0] = 1.0
+        Q[3, 1] = 1.0
+    else:
+        A = _navier_matrix(k, E_sub, nu_sub)
+        T, Z, sdim = scipy.linalg.schur(A, output="complex", sort="lhp")
+        assert sdim == 2, "substrate must have a two-dimensional decaying subspace"
+        Q = Z[:, :2]
+    S = Q
+    for h, E, nu in reversed(list(layers)):
+        if h > 0.0:
+            S = scipy.linalg.expm(-_navier_matrix(k, E, nu) * h) @ S
+    c = np.linalg.solve(S[2:4, :], np.array([0.0, -1.0], dtype=np.complex128))
+    return float((S @ c)[1].real)

@@ -97,3 +97,47 @@ def test_positive_operator_scan():
         k = np.geomspace(1e-3, 1e3, 61) / h
         v = K.khat_layered(k, h, E1, nu1, 1.0, nu2)
         assert np.all(v > 0) and np.all(np.isfinite(v))
+
+
+# ---- multi-layer stacks (the transfer-matrix generalisation of Eqs. 9/10) --------
+
+@pytest.mark.parametrize("kh", [0.05, 0.7, 3.0])
+def test_multilayer_one_layer_is_eq9(kh):
+    h, E1, nu1, E2, nu2 = 0.2, 3.0, 0.3, 1.0, 0.45
+    k = kh / h
+    ref = K.khat_layered(np.array([k]), h, E1, nu1, E2, nu2)[0]
+    assert K.khat_multilayer(k, [(h, E1, nu1)], E2, nu2) == pytest.approx(ref, rel=1e-11)
+
+
+@pytest.mark.parametrize("kh", [0.1, 1.0, 4.0])
+def test_multilayer_rigid_base_is_eq25(kh):
+    """One layer on a rigid base: 2 (1 - Lambda(kh)) / (E1* k), Lambda of Eq. (25)."""
+    h, E1, nu1 = 0.3, 2.0, 0.35
+    k = kh / h
+    ref = 2.0 * (1.0 - K.lam_rigid(kh, nu1)) / (K.e_star(E1, nu1) * k)
+    assert K.khat_multilayer(k, [(h, E1, nu1)], np.inf, 0.3) == pytest.approx(ref, rel=1e-10)
+
+
+def test_multilayer_split_layer_and_homogeneous_stack():
+    k = 2.5
+    one = K.khat_multilayer(k, [(0.5, 3.0, 0.3)], 1.0, 0.4)
+    split = K.khat_multilayer(k, [(0.2, 3.0, 0.3), (0.3, 3.0, 0.3), (0.0, 9.0, 0.2)], 1.0, 0.4)
+    assert split == pytest.approx(one, rel=1e-12)
+    same = K.khat_multilayer(k, [(0.1, 2.0, 0.3), (0.4, 2.0, 0.3)], 2.0, 0.3)
+    assert same == pytest.approx(K.khat_homogeneous(k, 2.0, 0.3), rel=1e-12)
+
+
+def test_multilayer_limits_and_ordering():
+    """High wave numbers see only the top layer (2/(E_top* k)); low ones the substrate
+    (2/(E_sub* k)); a stiff top layer over a soft one is stiffer than the reverse."""
+    layers = [(0.05, 5.0, 0.3), (0.1, 0.5, 0.25)]
+    k_hi = 40.0 / 0.05
+    assert K.khat_multilayer(k_hi, layers, 1.0, 0.3) == pytest.approx(
+        K.khat_homogeneous(k_hi, 5.0, 0.3), rel=1e-9)
+    k_lo = 1e-4
+    assert K.khat_multilayer(k_lo, layers, 1.0, 0.3) == pytest.approx(
+        K.khat_homogeneous(k_lo, 1.0, 0.3), rel=1e-3)
+    k = 10.0
+    stiff_top = K.khat_multilayer(k, layers, 1.0, 0.3)
+    soft_top = K.khat_multilayer(k, layers[::-1], 1.0, 0.3)
+    assert stiff_top < soft_top
