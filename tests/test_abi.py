@@ -109,3 +109,38 @@ def test_binding_signatures_match_header(bemlib):
         for i, (c, py) in enumerate(zip(params, fn.argtypes)):
             assert py in _expected(c), f"{name} argument {i}: header {c!r}, binding {py}"
         assert fn.restype in _expected(ret), f"{name} return: header {ret!r}, binding {fn.restype}"
+
+
+def test_argument_errors_before_any_device_call(bemlib):
+    """Entry points check their arguments before touching a device, so the statuses and
+    the thread's error message can be checked on a CPU host (no call here reaches CUDA)."""
+    import numpy as np
+    from paper_1807_01885_gb300 import bem
+    p = np.zeros((4, 4), np.float32)
+    u = np.zeros_like(p)
+    mat = (0.1, 1.0, 1.0, 0.3, 1.0, 0.3)           # delta, h, E1, nu1, E2, nu2
+    with pytest.raises(bem.BemError, match="power of two") as e:
+        bem.bem_matvec_static(512, *mat, p, u)
+    assert e.value.status == bem.BEM_EINVAL
+    with pytest.raises(bem.BemError, match="NULL") as e:
+        bem.bem_matvec_static(64, *mat, None, u)
+    assert e.value.status == bem.BEM_EINVAL
+    with pytest.raises(bem.BemError, match="invalid material") as e:
+        bem.bem_matvec_static(64, 0.1, 1.0, 1.0, 0.5, 1.0, 0.3, p, u)
+    assert e.value.status == bem.BEM_EINVAL
+    # batch: an empty batch is a no-op; a negative count is rejected with a message
+    st, res = bem.bem_solve_batch([], [], [])
+    assert st == bem.BEM_OK and res == []
+    assert bemlib.bem_solve_batch(-1, None, None, None, None, None) == bem.BEM_EINVAL
+    assert b"invalid batch" in bemlib.bem_last_error()
+    # network descriptor: widths from the list, modes >= 1, 1 <= layers <= 16
+    for kw in (dict(width=5), dict(hidden=3), dict(modes=0), dict(layers=0), dict(layers=17)):
+        args = dict(width=8, modes=2, layers=1, hidden=8)
+        args.update(kw)
+        with pytest.raises(bem.BemError) as e:
+            bem.Fno(**args)
+        assert e.value.status == bem.BEM_EINVAL, kw
+    # NULL handles: destroy is a no-op, the parameter count is -1
+    assert bemlib.bem_fno_param_count(None) == -1
+    assert bemlib.bem_fno_destroy(None) == bem.BEM_OK
+    assert bemlib.bem_destroy_kernel(None) == bem.BEM_OK
