@@ -36,12 +36,22 @@ class NoConvergence(RuntimeError):
     pass
 
 
+class NotPositiveDefinite(NoConvergence):
+    """A search direction with non-positive curvature t'Kt <= 0: the operator is not
+    positive definite on the contact set, the minimisation has no unique solution and
+    the conjugate-gradient steps are undefined (e.g. a negative DC value, reading of
+    the k = 0 term, on a period that is small compared with the coating)."""
+
+
 def _initial_depth_control(matvec, f, d):
     q = np.maximum(d - f, 0.0)
     if not np.any(q > 0):
         return np.zeros_like(f)
     Kq = matvec(q)
-    s = np.sum(q * (d - f)) / np.sum(q * Kq)
+    curv = np.sum(q * Kq)
+    if not curv > 0.0:
+        raise NotPositiveDefinite("non-positive curvature of the initial direction")
+    s = np.sum(q * (d - f)) / curv
     return s * q
 
 
@@ -99,7 +109,13 @@ def solve_nonadhesive(matvec, f, delta, control="depth", target=0.0, tol=1e-12,
         r = matvec(t)
         if load:
             r[Ic] -= r[Ic].mean()
-        tau = np.sum(g[Ic] * t[Ic]) / np.sum(r[Ic] * t[Ic])
+        curv = np.sum(r[Ic] * t[Ic])
+        if not np.any(t[Ic] != 0.0):
+            tau = 0.0                       # the gap is exactly level on the set: no step
+        elif not curv > 0.0:
+            raise NotPositiveDefinite(f"non-positive curvature t'Kt = {curv:.3e} at iteration {it}")
+        else:
+            tau = np.sum(g[Ic] * t[Ic]) / curv
         p = np.where(Ic, p - tau * t, p)
         neg = p < 0
         p[neg] = 0.0
@@ -153,7 +169,10 @@ def solve_fixed_set(matvec, C, b, tol=1e-13, max_iter=20000, p0=None):
         if np.sqrt(rr) <= tol * bnorm:
             return p, it
         Ks = np.where(C, matvec(s), 0.0)
-        a = rr / np.sum(s * Ks)
+        curv = np.sum(s * Ks)
+        if not curv > 0.0:
+            raise NotPositiveDefinite(f"non-positive curvature on the fixed set at iteration {it}")
+        a = rr / curv
         p = p + a * s
         r = r - a * Ks
         rr_new = np.sum(r * r)

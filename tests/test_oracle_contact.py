@@ -251,3 +251,24 @@ def test_force_controlled_pull_off_on_oracle_steps():
     # (3 % of the pull-off force allowed for that)
     assert F_min - 0.03 * abs(Fj) <= F_last < F_min + spacing + 0.03 * abs(Fj)
     assert F_last / Fj == pytest.approx(1.0, abs=0.15)
+
+
+def test_indefinite_operator_is_refused():
+    """Polonsky-Keer CG needs K positive definite on the contact set.  A thick stiff
+    coating (h = 10 a, E1/E2 = 10) on a 2N period makes the finite-part DC value of
+    the k = 0 term strongly negative (reading of Eq. 11 at k = 0) and K indefinite on
+    the punch: the dense matrix shows a negative eigenvalue, and the solve must stop
+    with NotPositiveDefinite instead of returning a pressure.  The same stack with
+    the literal DC rule (K^(0) = 0) stays positive definite and solves."""
+    N, delta, a = 64, 1.0, 16.0
+    f = inputs.flat_punch_height(N, delta, a)
+    C = (f == 0).ravel()
+    Kg, mv = _mv(N, delta, 10 * a, 10.0, 0.3, 1.0, 0.45)
+    assert Kg[0, 0] < 0
+    assert np.linalg.eigvalsh(operator.dense_matrix(Kg)[np.ix_(C, C)])[0] < 0
+    with pytest.raises(contact.NotPositiveDefinite):
+        contact.solve_nonadhesive(mv, f, delta, "depth", 1e-3 * a, tol=1e-12)
+    Kz, mz = _mv(N, delta, 10 * a, 10.0, 0.3, 1.0, 0.45, dc_mode=1)
+    assert np.linalg.eigvalsh(operator.dense_matrix(Kz)[np.ix_(C, C)])[0] > 0
+    s = contact.solve_nonadhesive(mz, f, delta, "depth", 1e-3 * a, tol=1e-12)
+    assert s["force"] > 0 and contact.kkt_violation(mz, s["p"], f, 1e-3 * a) < 1e-9
