@@ -126,7 +126,14 @@ __global__ void k_init_scale(const T* __restrict__ f, const T* __restrict__ q, c
   Acc<T> v[2] = {a0, a1};
   double tot[2];
   if (grid_reduce<2>(v, partials, ticket, tot)) {
-    st->scale = (tot[1] > 0.0) ? tot[0] / tot[1] : 0.0;
+    if (tot[0] > 0.0 && !(tot[1] > 0.0)) {
+      // q != 0 (q'(d - f) = |q|^2 > 0) with q'Kq <= 0: K is not positive definite on
+      // the cells of q, and the problem has no unique solution
+      st->scale = 0.0;
+      finish(st, BEM_ENAN);
+    } else {
+      st->scale = (tot[1] > 0.0) ? tot[0] / tot[1] : 0.0;   // q = 0: no contact at this depth
+    }
   }
 }
 
