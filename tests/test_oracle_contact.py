@@ -272,3 +272,35 @@ def test_indefinite_operator_is_refused():
     assert np.linalg.eigvalsh(operator.dense_matrix(Kz)[np.ix_(C, C)])[0] > 0
     s = contact.solve_nonadhesive(mz, f, delta, "depth", 1e-3 * a, tol=1e-12)
     assert s["force"] > 0 and contact.kkt_violation(mz, s["p"], f, 1e-3 * a) < 1e-9
+
+
+def test_flat_punch_stiffness_sweep_bracketed():
+    """Flat punch on a coating (L = 4a, N = 64, nu1 = 0.3, nu2 = 0.45), h/a in
+    {0.1, 0.3, 1, 3, 10}, E1/E2 in {0.1, 0.5, 2, 10}.  Stiffness F/d is normalised by
+    the same grid's homogeneous value (the period's images and the zero-mean datum
+    stiffen every punch alike, here by 1.43).  With the literal k = 0 rule (K^(0) = 0)
+    the operator stays ordered between the two homogeneous ones, so each normalised
+    stiffness lies between the substrate's and the coating's Boussinesq values
+    2aE2* and 2aE1*, moves monotonically from the first towards the second as h/a
+    grows, and reaches the coating's within 1 % at h/a = 10 (the layer then holds the
+    whole response at the window's scale)."""
+    N, delta, a = 64, 1.0, 16.0
+    f = inputs.flat_punch_height(N, delta, a)
+    E2, nu1, nu2 = 1.0, 0.3, 0.45
+    d = 1e-3 * a
+
+    def stiffness(h, E1, n1, Es, ns):
+        _, mv = _mv(N, delta, h, E1, n1, Es, ns, dc_mode=1)
+        return contact.solve_nonadhesive(mv, f, delta, "depth", d, tol=1e-12)["force"] / d
+
+    k_hom = stiffness(np.inf, 1.0, 0.3, 1.0, 0.3) / (2 * a * kernel.e_star(1.0, 0.3))
+    assert 1.2 < k_hom < 1.6
+    for r in (0.1, 0.5, 2.0, 10.0):
+        lo, hi = sorted([1.0, kernel.e_star(r, nu1) / kernel.e_star(E2, nu2)])
+        ks = [stiffness(hoa * a, r * E2, nu1, E2, nu2) / (k_hom * 2 * a * kernel.e_star(E2, nu2))
+              for hoa in (0.1, 0.3, 1.0, 3.0, 10.0)]
+        assert all(lo * (1 - 1e-6) <= k <= hi * (1 + 1e-6) for k in ks), (r, ks)
+        steps = np.diff(ks)
+        assert np.all(steps > 0) if r > 1 else np.all(steps < 0), (r, ks)
+        coat = kernel.e_star(r, nu1) / kernel.e_star(E2, nu2)
+        assert ks[-1] == pytest.approx(coat, rel=0.01), (r, ks)
