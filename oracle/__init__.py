@@ -23,6 +23,9 @@ analytic  closed forms used as pins: Hertz, JKR, flat punch (Eq. 4 based),
           thin-layer Eqs. (13)-(21), thick-layer series Eqs. (22)-(25).
 fno       FP64 Fourier-neural-operator forward/backward (naive truncated DFT),
           the reference for the warm-start network's kernels.
+influence the non-periodic operator of a homogeneous half-space: Love's closed-form
+          displacement of a uniformly loaded square cell, convolved over the open
+          plane (no k = 0 convention); no CUDA counterpart yet.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against
 closed forms, limits, invariants, brute force or an independent derivation; see
