@@ -86,3 +86,23 @@ def test_hertz_with_the_open_plane_operator():
     sp = contact.solve_nonadhesive(lambda p: operator.matvec_fft(Kg, p), f, delta, "force", F, tol=1e-12)
     assert sp["p"].max() / p0 == pytest.approx(1.0, abs=0.04)
     assert sp["d"] / d_H < 0.85
+
+
+def test_spectrum_fits_a_folded_real_table():
+    """The transform of the wrap-around coefficient array is real, even in each wave
+    index and symmetric between them, so the (N+1) x (N+1) quarter of it determines
+    the whole: the layout of the periodic product's compliance table."""
+    N, delta = 16, 1.0
+    G = influence.influence_love(N, delta, 1.0, 0.3)
+    M = 2 * N
+    W = np.zeros((M, M))
+    idx = np.arange(-(N - 1), N) % M
+    W[np.ix_(idx, idx)] = G
+    S = np.fft.fft2(W)
+    assert np.abs(S.imag).max() < 1e-12 * np.abs(S.real).max()
+    R = S.real
+    i = np.arange(M)
+    assert np.allclose(R, R[(-i) % M, :]) and np.allclose(R, R[:, (-i) % M]) and np.allclose(R, R.T)
+    Q = R[:N + 1, :N + 1]
+    fold = lambda k: np.minimum(k, M - k)
+    assert np.allclose(R, Q[fold(i)[:, None], fold(i)[None, :]])
