@@ -293,11 +293,11 @@ def test_flat_punch_stiffness_sweep_bracketed():
         _, mv = _mv(N, delta, h, E1, n1, Es, ns, dc_mode=1)
         return contact.solve_nonadhesive(mv, f, delta, "depth", d, tol=1e-12)["force"] / d
 
-    k_hom = stiffness(np.inf, 1.0, 0.3, 1.0, 0.3) / (2 * a * kernel.e_star(1.0, 0.3))
+    k_hom = stiffness(np.inf, 1.0, 0.3, 1.0, 0.3) / analytic.flat_punch_stiffness(a, kernel.e_star(1.0, 0.3))
     assert 1.2 < k_hom < 1.6
     for r in (0.1, 0.5, 2.0, 10.0):
         lo, hi = sorted([1.0, kernel.e_star(r, nu1) / kernel.e_star(E2, nu2)])
-        ks = [stiffness(hoa * a, r * E2, nu1, E2, nu2) / (k_hom * 2 * a * kernel.e_star(E2, nu2))
+        ks = [stiffness(hoa * a, r * E2, nu1, E2, nu2) / (k_hom * analytic.flat_punch_stiffness(a, kernel.e_star(E2, nu2)))
               for hoa in (0.1, 0.3, 1.0, 3.0, 10.0)]
         assert all(lo * (1 - 1e-6) <= k <= hi * (1 + 1e-6) for k in ks), (r, ks)
         steps = np.diff(ks)

@@ -106,3 +106,17 @@ def test_spectrum_fits_a_folded_real_table():
     Q = R[:N + 1, :N + 1]
     fold = lambda k: np.minimum(k, M - k)
     assert np.allclose(R, Q[fold(i)[:, None], fold(i)[None, :]])
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_flat_punch_stiffness_on_the_open_plane(N):
+    """Rigid flat punch of radius a = N/4 cells on a homogeneous half-space: the open
+    plane operator gives Boussinesq's F/d = 2 a E* (within 0.5 %), where the periodic
+    product of the same window is 43 % stiffer (its images and k = 0 datum)."""
+    delta, a, E, nu = 1.0, N / 4, 1.0, 0.3
+    f = inputs.flat_punch_height(N, delta, a)
+    G = influence.influence_love(N, delta, E, nu)
+    d = 1e-3 * a
+    s = contact.solve_nonadhesive(lambda p: influence.matvec_fft_np(G, p), f, delta, "depth", d, tol=1e-12)
+    k_B = analytic.flat_punch_stiffness(a, kernel.e_star(E, nu))
+    assert s["force"] / d / k_B == pytest.approx(1.0, abs=0.005)
