@@ -224,6 +224,20 @@ def bem_profile_passes(k, p, u, reps, stream=None):
 def bem_matvec_static(N, delta, h, E1, nu1, E2, nu2, p, u, dc_mode=BEM_DC_FINITE_PART, stream=None):
     """u = K p through the entry point that allocates nothing (float32 device arrays,
     N <= BEM_STATIC_MAX_N); for callers that may not allocate device memory."""
+    for name, x in (("p", p), ("u", u)):
+        if x is None:
+            continue
+        dtype = getattr(x, "dtype", None)
+        if str(dtype) not in ("torch.float32", "float32"):
+            raise ValueError(f"bem_matvec_static: {name} must be float32, got {dtype}")
+        size = x.numel() if hasattr(x, "numel") else x.size
+        if size != N * N:
+            raise ValueError(f"bem_matvec_static: {name} must hold N*N = {N * N} values, got {size}")
+        if hasattr(x, "device") and x.device.type == "cuda":
+            import torch
+            if x.device.index != torch.cuda.current_device():
+                raise ValueError(f"bem_matvec_static: {name} is on {x.device}, the current device is "
+                                 f"cuda:{torch.cuda.current_device()}")
     d = KernelDesc(N=N, precision=BEM_FP32, dc_mode=dc_mode, reserved=0, delta=delta, h=h, E1=E1, nu1=nu1,
                    E2=E2, nu2=nu2)
     _check(load().bem_matvec_static(ctypes.byref(d), _ptr(p), _ptr(u), _stream(stream)))

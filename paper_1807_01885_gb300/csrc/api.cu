@@ -32,17 +32,8 @@ bem_status solve_contact_device(bem_kernel_s* k, const bem_problem* prob, const 
 bem_status solve_batch_device(int n, bem_kernel_s* const* ks, const bem_problem* probs, const bool* has_pinit,
                               bem_result* res, cudaStream_t const* strm);
 
-namespace {
-
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
+// Argument checks of an operator description (shared with the allocation-free
+// entry point).
 bem_status check_desc(const bem_kernel_desc* d) {
   if (d == nullptr) { set_error("desc is NULL"); return BEM_EINVAL; }
   const int N = d->N;
@@ -61,6 +52,17 @@ bem_status check_desc(const bem_kernel_desc* d) {
     return BEM_EINVAL;
   }
   return BEM_OK;
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 bem_status check_problem(const bem_problem* prob) {

@@ -162,6 +162,8 @@ long long launches();
 // adds the durations of completed timed passes of k to its totals (host sync point)
 void harvest_pass_timing(const bem_kernel_s* k);
 bem_status cuda_fail(cudaError_t e, const char* what);
+// api.cu: BEM_OK when the description is valid, else BEM_EINVAL with a message
+bem_status check_desc(const bem_kernel_desc* d);
 
 // matvec.cu
 bem_status build_table(bem_kernel_s* k, cudaStream_t s);

@@ -71,13 +71,17 @@ bem_status scratch_address(int dev, void** out) {
   return BEM_OK;
 }
 
-bool on_device(const void* p) {
+// True for device (or managed) memory that belongs to device dev: the scratch array
+// and the stream the kernels run on are those of the current device, so an array of
+// another GPU would be read and written through peer access or fault.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -90,8 +94,11 @@ extern "C" bem_status bem_matvec_static(const bem_kernel_desc* desc, const float
     set_error("bem_matvec_static: NULL argument");
     return BEM_EINVAL;
   }
+  // the same operator checks as bem_make_kernel, then the limits of this entry point
+  bem_status st = check_desc(desc);
+  if (st != BEM_OK) return st;
   const int N = desc->N;
-  if (N < 4 || N > BEM_STATIC_MAX_N || (N & (N - 1))) {
+  if (N > BEM_STATIC_MAX_N) {
     set_error("bem_matvec_static: N must be a power of two in [4, " + std::to_string(BEM_STATIC_MAX_N) +
               "] (the fixed scratch array is sized for that); use bem_make_kernel/bem_matvec for larger grids");
     return BEM_EINVAL;
@@ -100,27 +107,19 @@ extern "C" bem_status bem_matvec_static(const bem_kernel_desc* desc, const float
     set_error("bem_matvec_static: only precision BEM_FP32 is available");
     return BEM_EINVAL;
   }
-  if (desc->dc_mode != BEM_DC_FINITE_PART && desc->dc_mode != BEM_DC_ZERO) {
-    set_error("bem_matvec_static: unknown dc_mode");
-    return BEM_EINVAL;
-  }
-  if (!(desc->delta > 0.0) || !(desc->h >= 0.0) || !(desc->E1 > 0.0) || !(desc->E2 > 0.0) ||
-      !(desc->nu1 >= 0.0 && desc->nu1 < 0.5) || !(desc->nu2 >= 0.0 && desc->nu2 < 0.5)) {
-    set_error("bem_matvec_static: invalid material or grid parameters");
-    return BEM_EINVAL;
-  }
   if (((uintptr_t)p & 15) != 0 || ((uintptr_t)u & 15) != 0) {
     set_error("bem_matvec_static: p and u must be 16-byte aligned");
     return BEM_EINVAL;
   }
-  if (!on_device(p) || !on_device(u)) {
-    set_error("bem_matvec_static: p and u must be device arrays (host arrays would need a staging allocation)");
-    return BEM_EINVAL;
-  }
   int dev = 0;
   BEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (!on_device(p, dev) || !on_device(u, dev)) {
+    set_error("bem_matvec_static: p and u must be device arrays of the current device (host arrays would need "
+              "a staging allocation)");
+    return BEM_EINVAL;
+  }
   void* base = nullptr;
-  bem_status st = scratch_address(dev, &base);
+  st = scratch_address(dev, &base);
   if (st != BEM_OK) return st;
   const StaticLayout lay(N);
   if (lay.total > kStaticBytes) {

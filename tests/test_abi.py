@@ -116,18 +116,32 @@ def test_argument_errors_before_any_device_call(bemlib):
     the thread's error message can be checked on a CPU host (no call here reaches CUDA)."""
     import numpy as np
     from paper_1807_01885_gb300 import bem
+    import ctypes
     p = np.zeros((4, 4), np.float32)
     u = np.zeros_like(p)
-    mat = (0.1, 1.0, 1.0, 0.3, 1.0, 0.3)           # delta, h, E1, nu1, E2, nu2
-    with pytest.raises(bem.BemError, match="power of two") as e:
-        bem.bem_matvec_static(512, *mat, p, u)
-    assert e.value.status == bem.BEM_EINVAL
-    with pytest.raises(bem.BemError, match="NULL") as e:
-        bem.bem_matvec_static(64, *mat, None, u)
-    assert e.value.status == bem.BEM_EINVAL
-    with pytest.raises(bem.BemError, match="invalid material") as e:
-        bem.bem_matvec_static(64, 0.1, 1.0, 1.0, 0.5, 1.0, 0.3, p, u)
-    assert e.value.status == bem.BEM_EINVAL
+
+    def static(N, p_, u_, nu1=0.3, E1=1.0, precision=bem.BEM_FP32):
+        d = bem.KernelDesc(N=N, precision=precision, dc_mode=0, reserved=0, delta=0.1, h=1.0, E1=E1, nu1=nu1,
+                           E2=1.0, nu2=0.3)
+        st = bemlib.bem_matvec_static(ctypes.byref(d), bem._ptr(p_), bem._ptr(u_), None)
+        return st, bemlib.bem_last_error().decode()
+
+    st, msg = static(512, p, u)
+    assert st == bem.BEM_EINVAL and "power of two" in msg and str(bem.BEM_STATIC_MAX_N) in msg
+    st, msg = static(64, None, u)
+    assert st == bem.BEM_EINVAL and "NULL" in msg
+    # the operator checks are those of bem_make_kernel (Poisson ratio, infinite E1)
+    st, msg = static(64, p, u, nu1=0.5)
+    assert st == bem.BEM_EINVAL and "Poisson" in msg
+    st, msg = static(64, p, u, E1=float("inf"))
+    assert st == bem.BEM_EINVAL and "E1" in msg
+    st, msg = static(64, p, u, precision=bem.BEM_FP64)
+    assert st == bem.BEM_EINVAL and "FP32" in msg
+    # the binding rejects a wrong dtype or size before the call
+    with pytest.raises(ValueError, match="float32"):
+        bem.bem_matvec_static(4, 0.1, 1.0, 1.0, 0.3, 1.0, 0.3, p.astype(np.float64), u)
+    with pytest.raises(ValueError, match="N\\*N"):
+        bem.bem_matvec_static(8, 0.1, 1.0, 1.0, 0.3, 1.0, 0.3, p, u)
     # batch: an empty batch is a no-op; a negative count is rejected with a message
     st, res = bem.bem_solve_batch([], [], [])
     assert st == bem.BEM_OK and res == []

@@ -246,9 +246,11 @@ def test_fft_nominal_flops(bench):
 def test_reference_arm_line_contract(bench, monkeypatch, capsys):
     """`bench.py --impl reference` prints one JSON line with the keys the benchmark
     contract needs; the oracle product is replaced by a fixed 0.5 s stand-in so the
-    line's arithmetic can be checked (a bounded sample: at most 6 timed products)."""
+    line's arithmetic can be checked.  Every requested step is timed and the line's
+    step counts are the ones that ran."""
     import json
-    monkeypatch.setattr(bench, "cpu_oracle_matvecs", lambda: 0.5)
+    calls = []
+    monkeypatch.setattr(bench, "cpu_oracle_matvecs", lambda: calls.append(1) or 0.5)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "40", "--warmup", "3"])
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     bench.run_reference(bench.parse())
@@ -263,7 +265,8 @@ def test_reference_arm_line_contract(bench, monkeypatch, capsys):
     assert d["higher_is_better"] is True and d["steps"] == 40 and d["warmup"] == 3
     assert "workload" in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "6 timed" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "40 timed" in cb["sample"]
+    assert len(calls) == 43
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

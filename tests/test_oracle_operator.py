@@ -86,3 +86,39 @@ def test_uniform_circular_load():
         u_r0 = 4 * P * r0 / (np.pi * Es) * (ellipe(m) - (1 - m) * ellipk(m))
         ref = 2 * P * b_eff / Es - u_r0
         assert u[c0, c0] - u[c0, c0 + r0] == pytest.approx(ref, rel=1e-2)
+
+
+STACKS = {
+    "layered": (0.35, 3.0, 0.3, 1.0, 0.45),
+    "rigid_base": (0.35, 1.0, 0.3, np.inf, 0.3),
+    "homogeneous": (np.inf, 2.0, 0.3, 2.0, 0.3),
+}
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+@pytest.mark.parametrize("dc_mode", [0, 1])
+@pytest.mark.parametrize("stack", sorted(STACKS))
+def test_influence_at_equals_inverse_dft(N, dc_mode, stack):
+    """``influence_at`` (one offset at a time, the reference of the full-size GPU
+    impulse test) against the naive 2-D inverse DFT of the same sampled compliance
+    (``influence``) at every offset (dy, dx) in (-N, N)^2, wrapped onto the 2N period,
+    and against the columns of the dense matrix of Eq. (1) (the response at every
+    window cell to a unit pressure on one cell).  A wrong wrap of negative offsets, a
+    wrong 1/M^2 factor or a wrong wave-number grid fails here."""
+    delta = 0.1
+    h, E1, nu1, E2, nu2 = STACKS[stack]
+    M = 2 * N
+    Kg = operator.khat_grid(N, delta, h, E1, nu1, E2, nu2, dc_mode=dc_mode)
+    G = operator.influence(Kg)
+    offs = [(dy, dx) for dy in range(-(N - 1), N) for dx in range(-(N - 1), N)]
+    got = operator.influence_at(N, delta, h, E1, nu1, E2, nu2, offs, dc_mode=dc_mode)
+    ref = np.array([G[dy % M, dx % M] for dy, dx in offs])
+    scale = abs(ref).max()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * scale)
+    # columns of the dense matrix: K[(r, c), (s, t)] = G(r - s, c - t)
+    Km = operator.dense_matrix(Kg)
+    for s, t in [(0, 0), (N - 1, 0), (N // 2, N - 1), (1, 2)]:
+        col = Km[:, s * N + t].reshape(N, N)
+        o = [(r - s, c - t) for r in range(N) for c in range(N)]
+        vals = operator.influence_at(N, delta, h, E1, nu1, E2, nu2, o, dc_mode=dc_mode).reshape(N, N)
+        np.testing.assert_allclose(vals, col, rtol=0, atol=1e-13 * scale)

@@ -24,6 +24,10 @@ TOL = 2e-6
     (256, dict(delta=1.0 / 256, h=8.0 / 256, E1=4.0, nu1=0.3, E2=1.0, nu2=0.45)),
     (64, dict(delta=0.01, h=float("inf"), E1=1.0, nu1=0.3, E2=1.0, nu2=0.3)),
     (16, dict(delta=0.1, h=0.2, E1=0.5, nu1=0.25, E2=float("inf"), nu2=0.3)),
+    # below 16 cells per side the product runs the shared-memory kernels on the
+    # blocked table layout, which the fixed array also holds
+    (8, dict(delta=0.2, h=0.3, E1=2.0, nu1=0.3, E2=1.0, nu2=0.3)),
+    (4, dict(delta=0.25, h=float("inf"), E1=1.0, nu1=0.2, E2=1.0, nu2=0.2)),
 ])
 def test_static_matches_handle_two_calls(cuda, N, params):
     g = torch.Generator(device=cuda).manual_seed(N)
@@ -62,3 +66,24 @@ def test_static_rejects_host_arrays(cuda):
     with pytest.raises(bem.BemError) as e:
         bem.bem_matvec_static(N, 0.1, 0.2, 1.0, 0.3, 1.0, 0.3, p, u)
     assert e.value.status == bem.BEM_EINVAL
+
+
+def test_static_calls_allocate_nothing(cuda):
+    """After one warm-up call per grid size (the first call looks up the fixed array's
+    address and sets kernel attributes), further calls leave the device's free memory
+    unchanged: the product's intermediates live in the fixed array only."""
+    params = dict(delta=1.0 / 256, h=8.0 / 256, E1=4.0, nu1=0.3, E2=1.0, nu2=0.45)
+    bufs = {}
+    for N in (8, 256):
+        p = torch.rand((N, N), dtype=torch.float32, device=cuda)
+        u = torch.empty_like(p)
+        bem.bem_matvec_static(N, p=p, u=u, **params)
+        bufs[N] = (p, u)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for N, (p, u) in bufs.items():
+            bem.bem_matvec_static(N, p=p, u=u, **params)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
