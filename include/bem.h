@@ -114,6 +114,28 @@ typedef struct {
 bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out);
 bem_status bem_destroy_kernel(bem_kernel k);
 
+/* One layer of a coating stack: thickness, Young's modulus, Poisson ratio. */
+#define BEM_MAX_LAYERS 8
+typedef struct {
+  double h, E, nu;
+} bem_layer;
+
+/* Builds the operator of a stack of n_layers (1..BEM_MAX_LAYERS) bonded layers,
+ * listed from the surface down, on the substrate (desc->E2, desc->nu2; E2 = INFINITY
+ * is a rigid base): the multi-layer generalisation of Eqs. (9)/(10), which the paper
+ * gives for one layer.  The compliance follows from Eq. (5) with boundary conditions
+ * (a)-(d) of Sec. 2 at the surface and at every interface, evaluated in double for
+ * every |k| of the grid; the k = 0 entry is the finite part lim_{k->0}[K(k) - 2/(E2* k)]
+ * (dc_mode 0; for a rigid base the stack's uniaxial compliance sum h/E~) or 0
+ * (dc_mode 1).  desc->N, precision, dc_mode, delta, E2 and nu2 are used as in
+ * bem_make_kernel; desc->h, E1 and nu1 are ignored and replaced, in the handle, by the
+ * stack's total thickness and the top layer's E and nu (the top layer sets the
+ * detachment stress of Eq. 12).  Each layer needs 0 <= h < INFINITY, 0 < E < INFINITY,
+ * 0 <= nu < 0.5, and the stack a positive total thickness; else BEM_EINVAL.  One
+ * layer gives the table of bem_make_kernel with the same h, E1, nu1 (to rounding). */
+bem_status bem_make_kernel_layers(const bem_kernel_desc* desc, int32_t n_layers, const bem_layer* layers,
+                                  void* cuda_stream, bem_kernel* out);
+
 /* Copies the double-precision compliance table K^(k_ij), i, j in [0, N], row-major
  * (N+1)*(N+1) doubles, in m/Pa-consistent units (no FFT normalisation), to out
  * (host or device).  Entry (0,0) is the DC value chosen by dc_mode. */

@@ -11,6 +11,10 @@ Test infrastructure (see ``oracle/__init__``).  Plain FP64 numpy.
   paper's Eq. (11) is defined for k != 0 only, so the value at k = 0 is a reading:
   the finite part lim_{k->0} [K^(k) - 2/(E2* k)]).
 * ``lam_rigid``          Eq. (25): Lambda(u), L = 4 nu - 3.
+* ``khat_multilayer``     the same transfer-matrix solve for a stack of layers on a
+  substrate (the multi-layer generalisation of Eqs. 9/10); ``khat_multilayer_mp``
+  the same in mpmath arithmetic, and ``khat_multilayer_dc`` its k -> 0 finite part
+  by Richardson extrapolation in that arithmetic.
 * ``khat_transfer_matrix``  an independent derivation: Eq. (5) written as a
   first-order system in (u_k, u_z, sigma_kz, sigma_zz), propagated through the layer
   by a matrix exponential, with the decaying invariant subspace of the half-space
@@ -199,3 +203,71 @@ def khat_multilayer(k, layers, E_sub, nu_sub):
             S = scipy.linalg.expm(-_navier_matrix(k, E, nu) * h) @ S
     c = np.linalg.solve(S[2:4, :], np.array([0.0, -1.0], dtype=np.complex128))
     return float((S @ c)[1].real)
+
+
+def _navier_matrix_mp(k, E, nu):
+    """``_navier_matrix`` in mpmath arithmetic (same first-order system of Eq. 5)."""
+    import mpmath as mp
+    E, nu, k = mp.mpf(E), mp.mpf(nu), mp.mpf(k)
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    ik = mp.mpc(0, 1) * k
+    M = mp.zeros(4, 4)
+    M[0, 1] = -ik
+    M[0, 2] = 1 / mu
+    M[1, 0] = -lam * ik / (lam + 2 * mu)
+    M[1, 3] = 1 / (lam + 2 * mu)
+    for j in range(4):
+        M[2, j] = -ik * lam * M[1, j]
+    M[2, 0] += k * k * (lam + 2 * mu)
+    M[3, 2] = -ik
+    return M
+
+
+def khat_multilayer_mp(k, layers, E_sub, nu_sub, dps=50):
+    """``khat_multilayer`` evaluated in mpmath with ``dps`` digits, for the long-wave
+    limit below.  The substrate's decaying subspace is found without a Schur form:
+    its system matrix A has the eigenvalues +k and -k, each twice (one Jordan block
+    each), so (A - k I)^2 vanishes on the growing pair and maps the whole space onto
+    the decaying pair; two fixed generic combinations of its columns span it."""
+    import mpmath as mp
+    with mp.workdps(dps):
+        k = mp.mpf(k)
+        if np.isinf(E_sub):
+            S = mp.zeros(4, 2)
+            S[2, 0] = 1
+            S[3, 1] = 1
+        else:
+            A = _navier_matrix_mp(k, E_sub, nu_sub)
+            B = A - k * mp.eye(4)
+            R = mp.matrix([[1, 0.37], [0.29, 1], [-0.53, 0.61], [0.71, -0.43]])
+            S = (B * B) * R
+        for h, E, nu in reversed(list(layers)):
+            if h > 0.0:
+                S = mp.expm(-_navier_matrix_mp(k, E, nu) * mp.mpf(h)) * S
+        T = mp.matrix([[S[2, 0], S[2, 1]], [S[3, 0], S[3, 1]]])
+        c = mp.lu_solve(T, mp.matrix([0, -1]))
+        uz = S[1, 0] * c[0] + S[1, 1] * c[1]
+        return mp.re(uz)
+
+
+def khat_multilayer_dc(layers, E_sub, nu_sub, levels=5, dps=50):
+    """Finite part lim_{k->0} [K(k) - 2/(E_sub* k)] of the stack's compliance (the
+    same k = 0 reading as ``khat_dc``; 2/(E_sub* k) is absent for a rigid base).
+    phi(k) = k K(k) = phi(0) + phi'(0) k + ..., and the finite part is phi'(0),
+    taken by Richardson extrapolation of (phi(k) - phi(0))/k over k = k0/2^i with
+    k0 times the stack's thickness 1e-6, in ``dps``-digit arithmetic so that the
+    difference keeps its digits."""
+    import mpmath as mp
+    H = sum(h for h, _, _ in layers)
+    with mp.workdps(dps):
+        phi0 = mp.mpf(0) if np.isinf(E_sub) else 2 * (1 - mp.mpf(nu_sub) ** 2) / mp.mpf(E_sub)
+        k0 = mp.mpf("1e-6") / mp.mpf(H)
+        T = []
+        for i in range(levels):
+            kk = k0 / 2 ** i
+            T.append([(kk * khat_multilayer_mp(kk, layers, E_sub, nu_sub, dps) - phi0) / kk])
+        for j in range(1, levels):
+            for i in range(j, levels):
+                T[i].append((2 ** j * T[i][j - 1] - T[i - 1][j - 1]) / (2 ** j - 1))
+        return float(T[-1][-1])

@@ -12,6 +12,8 @@ term takes the finite part of ``kernel.khat_dc`` (or 0 with dc_mode=1, the liter
 "no DC component" rule), and u is read back on the window.
 
 * ``khat_grid``     the sampled compliance on the full M x M grid.
+* ``khat_grid_layers``  the same for a stack of layers on a substrate
+                    (``kernel.khat_multilayer`` at every distinct |k|).
 * ``influence``     G(x) = (1/M^2) sum_k K(k) e^{i k.x}, by the naive 2-D inverse DFT.
 * ``dense_matrix``  the N^2 x N^2 matrix K of Eq. (1): K[r, s] = G(x_r - x_s).
 * ``matvec_dense``  Eq. (1) as a dense product (O(N^4); tiny N only).
@@ -45,6 +47,27 @@ def khat_grid(N, delta, h, E1, nu1, E2, nu2, dc_mode=0):
         K[0, 0] = _kernel.khat_dc(h, E1, nu1, E2, nu2)
     else:
         K[0, 0] = 0.0
+    return K
+
+
+def khat_grid_layers(N, delta, layers, E_sub, nu_sub, dc_mode=0, dc_value=None):
+    """Compliance of a stack of bonded layers (``layers``: (h, E, nu) from the surface
+    down) on a substrate (E_sub = inf: rigid base) sampled on the padded grid, with the
+    same k = 0 reading as ``khat_grid``: the finite part (``kernel.khat_multilayer_dc``,
+    or ``dc_value`` when the caller has it already) or 0 (dc_mode=1).  Each distinct
+    |k| is evaluated once (K depends on i^2 + j^2 only)."""
+    M = 2 * N
+    i = np.arange(M)
+    it = np.where(i <= N, i, i - M)
+    sq = it[:, None] ** 2 + it[None, :] ** 2
+    K = np.zeros((M, M))
+    for s2 in np.unique(sq):
+        if s2 == 0:
+            continue
+        k = 2.0 * np.pi * np.sqrt(float(s2)) / (M * delta)
+        K[sq == s2] = _kernel.khat_multilayer(k, layers, E_sub, nu_sub)
+    if dc_mode == 0:
+        K[0, 0] = dc_value if dc_value is not None else _kernel.khat_multilayer_dc(layers, E_sub, nu_sub)
     return K
 
 

@@ -30,7 +30,8 @@ EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_mat
            "bem_launch_count", "bem_last_error", "bem_version", "bem_fno_create", "bem_fno_destroy",
            "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features", "bem_fno_forward",
            "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure", "bem_set_radix",
-           "bem_autotune")
+           "bem_autotune", "bem_make_kernel_layers")
+BEM_MAX_LAYERS = 8
 BEM_STATIC_MAX_N = 256
 
 
@@ -44,6 +45,10 @@ class KernelDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("precision", ctypes.c_int32), ("dc_mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("delta", ctypes.c_double), ("h", ctypes.c_double),
                 ("E1", ctypes.c_double), ("nu1", ctypes.c_double), ("E2", ctypes.c_double), ("nu2", ctypes.c_double)]
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("E", ctypes.c_double), ("nu", ctypes.c_double)]
 
 
 class FnoDesc(ctypes.Structure):
@@ -82,6 +87,9 @@ def load(path=None):
     lib = ctypes.CDLL(path)
     vp, i32 = ctypes.c_void_p, ctypes.c_int32
     lib.bem_make_kernel.argtypes = [ctypes.POINTER(KernelDesc), vp, ctypes.POINTER(vp)]
+    lib.bem_make_kernel_layers.argtypes = [ctypes.POINTER(KernelDesc), i32, ctypes.POINTER(Layer), vp,
+                                           ctypes.POINTER(vp)]
+    lib.bem_make_kernel_layers.restype = i32
     lib.bem_destroy_kernel.argtypes = [vp]
     lib.bem_kernel_table.argtypes = [vp, vp, vp]
     lib.bem_matvec.argtypes = [vp, vp, vp, vp]
@@ -171,6 +179,19 @@ def bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, precision=BEM_FP64, dc_mode=B
                    E2=E2, nu2=nu2)
     out = ctypes.c_void_p()
     _check(lib.bem_make_kernel(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def bem_make_kernel_layers(N, delta, layers, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART, stream=None):
+    """Operator of a stack of bonded layers ``layers`` = [(h, E, nu), ...] from the
+    surface down, on the substrate (E2, nu2)."""
+    lib = load()
+    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, reserved=0, delta=delta, h=0.0, E1=1.0, nu1=0.0,
+                   E2=E2, nu2=nu2)
+    n = len(layers)
+    arr = (Layer * max(n, 1))(*[Layer(h=float(h), E=float(E), nu=float(nu)) for h, E, nu in layers])
+    out = ctypes.c_void_p()
+    _check(lib.bem_make_kernel_layers(ctypes.byref(d), n, arr, _stream(stream), ctypes.byref(out)))
     return out.value
 
 
@@ -276,12 +297,19 @@ def bem_launch_count():
 class Kernel:
     """Owning wrapper of a bem_kernel handle (same parameters as bem_kernel_desc)."""
 
-    def __init__(self, N, delta, h, E1, nu1, E2, nu2, precision="fp64", dc_mode=BEM_DC_FINITE_PART, stream=None):
+    def __init__(self, N, delta, h=None, E1=None, nu1=None, E2=1.0, nu2=0.3, precision="fp64",
+                 dc_mode=BEM_DC_FINITE_PART, stream=None, layers=None):
+        """One coating (h, E1, nu1) on the substrate (E2, nu2), or, with ``layers`` =
+        [(h, E, nu), ...] from the surface down, a stack of coatings on it."""
         self.N, self.delta = N, delta
-        self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
         self.precision = precision
         prec = BEM_FP64 if precision == "fp64" else BEM_FP32
-        self.handle = bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream)
+        if layers is not None:
+            self.params = dict(layers=[tuple(x) for x in layers], E2=E2, nu2=nu2)
+            self.handle = bem_make_kernel_layers(N, delta, layers, E2, nu2, prec, dc_mode, stream)
+        else:
+            self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
+            self.handle = bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream)
 
     @property
     def torch_dtype(self):

@@ -334,13 +334,39 @@ bem_status bem_autotune(bem_kernel k, int32_t reps, int32_t* choice_out, void* c
   return BEM_OK;
 }
 
-bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out) {
+static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, const bem_layer* layers,
+                              void* cuda_stream, bem_kernel* out) {
   if (out == nullptr) { set_error("out is NULL"); return BEM_EINVAL; }
   *out = nullptr;
+  bem_kernel_desc dd;
+  if (n_layers > 0) {
+    if (desc == nullptr || layers == nullptr) { set_error("NULL desc or layer list"); return BEM_EINVAL; }
+    if (n_layers > BEM_MAX_LAYERS) { set_error("at most BEM_MAX_LAYERS layers"); return BEM_EINVAL; }
+    double H = 0.0;
+    for (int l = 0; l < n_layers; ++l) {
+      const bem_layer& L = layers[l];
+      if (!(L.h >= 0.0) || !isfinite(L.h) || !(L.E > 0.0) || !isfinite(L.E) || !(L.nu >= 0.0 && L.nu < 0.5)) {
+        set_error("layer " + std::to_string(l) + ": needs 0 <= h < inf, 0 < E < inf, 0 <= nu < 0.5");
+        return BEM_EINVAL;
+      }
+      H += L.h;
+    }
+    if (!(H > 0.0)) { set_error("the layer stack needs a positive total thickness"); return BEM_EINVAL; }
+    dd = *desc;
+    dd.h = H;
+    dd.E1 = layers[0].E;
+    dd.nu1 = layers[0].nu;
+    desc = &dd;
+  } else if (n_layers < 0) {
+    set_error("negative layer count");
+    return BEM_EINVAL;
+  }
   bem_status st = check_desc(desc);
   if (st != BEM_OK) return st;
   bem_kernel_s* k = new bem_kernel_s();
   k->desc = *desc;
+  k->n_layers = n_layers;
+  for (int l = 0; l < n_layers; ++l) k->layers[l] = layers[l];
   k->N = desc->N;
   k->M = 2 * desc->N;
   k->logN = 0;
@@ -394,6 +420,20 @@ bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_k
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "build_table");
   *out = k;
   return BEM_OK;
+}
+
+bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out) {
+  return make_kernel(desc, 0, nullptr, cuda_stream, out);
+}
+
+bem_status bem_make_kernel_layers(const bem_kernel_desc* desc, int32_t n_layers, const bem_layer* layers,
+                                  void* cuda_stream, bem_kernel* out) {
+  if (n_layers < 1) {
+    if (out != nullptr) *out = nullptr;
+    set_error("bem_make_kernel_layers needs 1 <= n_layers <= BEM_MAX_LAYERS");
+    return BEM_EINVAL;
+  }
+  return make_kernel(desc, n_layers, layers, cuda_stream, out);
 }
 
 bem_status bem_destroy_kernel(bem_kernel k) {

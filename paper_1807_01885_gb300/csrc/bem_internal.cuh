@@ -118,6 +118,8 @@ struct bem_kernel_s {
   int prec;       // BEM_FP64 / BEM_FP32
   size_t elem;    // sizeof(real)
   int dev;
+  int n_layers = 0;    // > 0: coating stack of bem_make_kernel_layers (replaces h, E1, nu1)
+  bem_layer layers[BEM_MAX_LAYERS];
   int col_radix_alt;   // 1: radix 8 for the float column pass (bem_set_radix, bem_autotune)
   int row_radix_alt;   // 1: radix 8 for the float row passes (bem_set_radix, bem_autotune)
   bem::Workspace ws;

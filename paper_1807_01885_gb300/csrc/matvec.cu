@@ -18,6 +18,7 @@
 
 #include "bem_internal.cuh"
 #include "fft.cuh"
+#include "stack.cuh"
 
 namespace bem {
 
@@ -54,6 +55,39 @@ __global__ void k_table64(double* __restrict__ t64, KernelParams P) {
     }
   }
   t64[(size_t)i * (P.N + 1) + j] = val;
+}
+
+// Compliance of a coating stack (stack.cuh) for every (i, j) in [0, N]^2; the
+// k = 0 entry is the finite part computed on the host.
+__global__ void k_table64_stack(double* __restrict__ t64, Stack st, double kstep, double dc, int N) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j > N) return;
+  double val;
+  if (i == 0 && j == 0) {
+    val = dc;
+  } else {
+    const double k = kstep * sqrt((double)(i * i + j * j));
+    val = stack_phi<double>(st, k) / k;
+  }
+  t64[(size_t)i * (N + 1) + j] = val;
+}
+
+// The stack of a handle in the scaled form of stack.cuh.
+static Stack stack_of(const bem_kernel_s* k) {
+  Stack st{};
+  st.n = k->n_layers;
+  const double mu_ref = k->layers[0].E / (2.0 * (1.0 + k->layers[0].nu));
+  st.mu_ref = mu_ref;
+  for (int l = 0; l < st.n; ++l) {
+    st.L[l].h = k->layers[l].h;
+    st.L[l].q = k->layers[l].E / (2.0 * (1.0 + k->layers[l].nu)) / mu_ref;
+    st.L[l].nu = k->layers[l].nu;
+  }
+  st.rigid = isinf(k->desc.E2) ? 1 : 0;
+  st.qs = st.rigid ? 0.0 : k->desc.E2 / (2.0 * (1.0 + k->desc.nu2)) / mu_ref;
+  st.nus = k->desc.nu2;
+  return st;
 }
 
 // Blocked copy in the path precision, scaled by 1/M^2:
@@ -149,7 +183,18 @@ bem_status build_table(bem_kernel_s* k, cudaStream_t s) {
     P.dc = P.c_pref * d.h * (dn * d0 - n0 * dd) / (d0 * d0);
   }
   dim3 grid((k->N + 1 + 127) / 128, k->N + 1);
-  k_table64<<<grid, 128, 0, s>>>(k->ws.table64, P);
+  if (k->n_layers > 0) {
+    // stack: the long-wave expansion phi(eps) = phi(0) + phi'(0) eps by dual numbers
+    const Stack st = stack_of(k);
+    const double dc = (d.dc_mode == BEM_DC_ZERO) ? 0.0 : stack_phi<Dual>(st, Dual{0.0, 1.0}).d;
+    if (!isfinite(dc)) {
+      set_error("coating stack: non-finite long-wave compliance");
+      return BEM_EINVAL;
+    }
+    k_table64_stack<<<grid, 128, 0, s>>>(k->ws.table64, st, P.kstep, dc, k->N);
+  } else {
+    k_table64<<<grid, 128, 0, s>>>(k->ws.table64, P);
+  }
   note_launches(3);
   BEM_CUDA_TRY(cudaGetLastError());
   const double scale = 1.0 / ((double)k->M * (double)k->M);

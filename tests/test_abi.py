@@ -34,6 +34,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(bem.KernelDesc) == 4 * 4 + 6 * 8
     assert ctypes.sizeof(bem.Problem) == 3 * 8 + 2 * 4 + 3 * 8
     assert ctypes.sizeof(bem.Result) == 6 * 8 + 6 * 4
+    assert ctypes.sizeof(bem.Layer) == 3 * 8
 
 
 def test_invalid_descriptor_rejected_without_gpu(bemlib):
@@ -75,7 +76,7 @@ def _expected(ctype):
     scalars = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "float": ctypes.c_float,
                "double": ctypes.c_double, "bem_status": ctypes.c_int32, "const char*": ctypes.c_char_p}
     structs = {"bem_kernel_desc": bem.KernelDesc, "bem_problem": bem.Problem, "bem_result": bem.Result,
-               "bem_fno_desc": getattr(bem, "FnoDesc", None)}
+               "bem_fno_desc": getattr(bem, "FnoDesc", None), "bem_layer": bem.Layer}
     t = " ".join(ctype.replace("*", " * ").split())
     t = t.replace(" *", "*")
     if t in scalars:
@@ -142,6 +143,14 @@ def test_argument_errors_before_any_device_call(bemlib):
         bem.bem_matvec_static(4, 0.1, 1.0, 1.0, 0.3, 1.0, 0.3, p.astype(np.float64), u)
     with pytest.raises(ValueError, match="N\\*N"):
         bem.bem_matvec_static(8, 0.1, 1.0, 1.0, 0.3, 1.0, 0.3, p, u)
+    # coating stacks: layer count, thickness, modulus, Poisson ratio, total thickness
+    for layers, msg in (([], "n_layers"), ([(0.1, 1.0, 0.3)] * 9, "BEM_MAX_LAYERS"),
+                        ([(0.1, 1.0, 0.3), (-0.1, 1.0, 0.3)], "layer 1"),
+                        ([(0.1, float("inf"), 0.3)], "layer 0"), ([(0.1, 1.0, 0.5)], "layer 0"),
+                        ([(0.0, 1.0, 0.3)], "total thickness")):
+        with pytest.raises(bem.BemError, match=msg) as e:
+            bem.bem_make_kernel_layers(16, 0.1, layers, 1.0, 0.3)
+        assert e.value.status == bem.BEM_EINVAL
     # batch: an empty batch is a no-op; a negative count is rejected with a message
     st, res = bem.bem_solve_batch([], [], [])
     assert st == bem.BEM_OK and res == []

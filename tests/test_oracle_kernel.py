@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import kernel as K
+from oracle import kernel
 
 PARAMS = [  # (h, E1, nu1, E2, nu2)
     (1.0, 4.0, 0.3, 1.0, 0.3),
@@ -141,3 +142,63 @@ def test_multilayer_limits_and_ordering():
     stiff_top = K.khat_multilayer(k, layers, 1.0, 0.3)
     soft_top = K.khat_multilayer(k, layers[::-1], 1.0, 0.3)
     assert stiff_top < soft_top
+
+
+@pytest.mark.parametrize("stack", [(0.35, 3.0, 0.3, 1.0, 0.45), (0.8, 0.2, 0.45, 1.0, 0.3), (0.35, 1.0, 0.3, np.inf, 0.3)])
+def test_multilayer_dc_one_layer_is_eq9_finite_part(stack):
+    """The stack's long-wave finite part (Richardson extrapolation in mpmath) reduces,
+    for one layer, to the closed-form finite part of Eq. (9)."""
+    h, E1, nu1, E2, nu2 = stack
+    assert kernel.khat_multilayer_dc([(h, E1, nu1)], E2, nu2) == pytest.approx(
+        kernel.khat_dc(h, E1, nu1, E2, nu2), rel=1e-12, abs=1e-15)
+
+
+def test_multilayer_dc_rigid_base_is_uniaxial_compression():
+    """On a rigid base a uniform pressure compresses each layer in uniaxial strain
+    (no lateral expansion over an infinite wavelength): K(0) = sum h_j / E~_j, the
+    thin-layer modulus of Eq. (15) per layer."""
+    layers = [(0.1, 0.8, 0.25), (0.15, 4.0, 0.35), (0.3, 1.5, 0.3)]
+    ref = sum(h / kernel.e_tilde(E, nu) for h, E, nu in layers)
+    assert kernel.khat_multilayer_dc(layers, np.inf, 0.3) == pytest.approx(ref, rel=1e-13)
+
+
+def test_multilayer_dc_split_and_substrate_layer():
+    """Splitting a layer in two of the same material, or adding a layer of the
+    substrate's own material below the stack, leaves the finite part unchanged."""
+    base = kernel.khat_multilayer_dc([(0.2, 3.0, 0.3), (0.5, 0.5, 0.4)], 1.0, 0.45)
+    split = kernel.khat_multilayer_dc([(0.2, 3.0, 0.3), (0.2, 0.5, 0.4), (0.3, 0.5, 0.4)], 1.0, 0.45)
+    below = kernel.khat_multilayer_dc([(0.2, 3.0, 0.3), (0.5, 0.5, 0.4), (0.4, 1.0, 0.45)], 1.0, 0.45)
+    assert split == pytest.approx(base, rel=1e-12)
+    assert below == pytest.approx(base, rel=1e-12)
+    # a stack of the substrate's material is the homogeneous half-space: finite part 0
+    assert abs(kernel.khat_multilayer_dc([(0.3, 1.0, 0.45)], 1.0, 0.45)) < 1e-13
+
+
+def test_multilayer_mp_matches_double():
+    layers = [(0.2, 3.0, 0.3), (0.5, 0.5, 0.4)]
+    for k in (0.05, 0.7, 9.0):
+        for Es in (1.0, np.inf):
+            assert float(kernel.khat_multilayer_mp(k, layers, Es, 0.45)) == pytest.approx(
+                kernel.khat_multilayer(k, layers, Es, 0.45), rel=1e-12)
+
+
+def test_multilayer_grid_one_layer_equals_eq9_grid():
+    from oracle import operator
+    N, d = 8, 0.1
+    a = operator.khat_grid_layers(N, d, [(0.35, 3.0, 0.3)], 1.0, 0.45)
+    b = operator.khat_grid(N, d, 0.35, 3.0, 0.3, 1.0, 0.45)
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+def test_multilayer_golden_file_is_current():
+    """tests/golden/multilayer_dc.json (read by the GPU tests, whose box has no mpmath)
+    holds what the oracle computes now."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_multilayer_dc
+    stored = json.load(open(os.path.join(here, "multilayer_dc.json")))
+    for name, (layers, Es, nus) in make_multilayer_dc.STACKS.items():
+        assert stored[name]["dc"] == pytest.approx(kernel.khat_multilayer_dc(layers, Es, nus), rel=1e-13), name
