@@ -56,6 +56,8 @@ def parse():
                     help="training solutions for the learned warm start (0: skip)")
     ap.add_argument("--adhesive", type=int, default=1,
                     help="run the adhesive ramp workload (N=512, 200 steps, FP32; 0: skip)")
+    ap.add_argument("--punch", type=int, default=1,
+                    help="run the flat-punch stiffness sweep (N=256, 20 cells, FP64 and FP32; 0: skip)")
     ap.add_argument("--radix", default=None, metavar="ROWS,COLS",
                     help="log2 FFT radices to use instead of the autotuner's choice (e.g. 4,4); for "
                          "profiling runs, where the autotuner's timings would be taken under the profiler")
@@ -374,6 +376,51 @@ def adhesive_bench(torch, dev, bem, inputs):
             "all_converged": all(r["status"] == 0 for r in out),
             "contact_lost_after_step": int(max([i for i, r in enumerate(out) if r["n_contact"] > 0], default=-1)),
             "dtype": "f32", "tabor": mu}
+
+
+def punch_sweep_bench(torch, dev, bem, inputs):
+    """Flat-punch stiffness sweep: rigid cylindrical punch of radius a = 64 cells on a
+    coating, L = 4a, N = 256, nu1 = 0.3, nu2 = 0.45, h/a in {0.1, 0.3, 1, 3, 10} x E1/E2
+    in {0.1, 0.5, 2, 10}, depth control, FP64 and FP32 (literal k = 0 rule).  Stiffness
+    F/d normalised by the same grid's homogeneous punch and by 2aE2*; wall time of the
+    20 solves per precision (tables built inside the timed loop, one handle per cell)."""
+    N, delta, a = 256, 1.0, 64.0
+    E2, nu1, nu2 = 1.0, 0.3, 0.45
+    d = 1e-3 * a
+    hoa, ratios = (0.1, 0.3, 1.0, 3.0, 10.0), (0.1, 0.5, 2.0, 10.0)
+    f = inputs.flat_punch_height(N, delta, a)
+    es2 = E2 / (1 - nu2 * nu2)
+    out = {"N": N, "a_cells": a, "h_over_a": list(hoa), "E1_over_E2": list(ratios), "dc_mode": 1}
+    s = torch.cuda.Stream(device=dev)
+    for precision, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        fd = torch.tensor(f, device=dev, dtype=dt)
+        tol = 1e-12 if precision == "fp64" else 1e-8
+
+        def stiff(h, E1, n1, Es, ns):
+            with bem.Kernel(N, delta, h, E1, n1, Es, ns, precision=precision, dc_mode=bem.BEM_DC_ZERO,
+                            stream=s) as k:
+                _, res = k.solve(fd, "depth", d, tol=tol, stream=s)
+            return res["force"] / d, res["status"]
+
+        k_hom, _ = stiff(np.inf, 1.0, 0.3, 1.0, 0.3)
+        norm = k_hom / (2 * a * 1.0 / (1 - 0.09))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        table, ok = [], True
+        for r in ratios:
+            row = []
+            for x in hoa:
+                kv, st = stiff(x * a, r * E2, nu1, E2, nu2)
+                ok = ok and st == 0
+                row.append(kv / (norm * 2 * a * es2))
+            table.append(row)
+        torch.cuda.synchronize()
+        out[precision] = {"wall_ms": 1000 * (time.perf_counter() - t0), "solves": len(ratios) * len(hoa),
+                          "stiffness_over_2aE2star": table, "homogeneous_grid_factor": norm, "all_converged": ok}
+    out["fp32_vs_fp64_max_rel"] = float(max(abs(a_ / b_ - 1) for ra, rb in zip(out["fp32"]["stiffness_over_2aE2star"],
+                                                                             out["fp64"]["stiffness_over_2aE2star"])
+                                        for a_, b_ in zip(ra, rb)))
+    return out
 
 
 WS_TRAIN_SEED0 = 30000000
@@ -722,6 +769,8 @@ def run_ours(args):
         line["batch"] = batch_bench(torch, dev, bem, inputs, args.batch, radix)
     if args.adhesive > 0:
         line["adhesive_ramp"] = adhesive_bench(torch, dev, bem, inputs)
+    if args.punch > 0:
+        line["punch_sweep"] = punch_sweep_bench(torch, dev, bem, inputs)
     if args.warmstart > 0:
         line["warm_start"] = warm_start_bench(torch, dev, bem, args.warmstart, 1500, 2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

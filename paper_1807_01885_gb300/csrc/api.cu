@@ -31,6 +31,7 @@ bem_status solve_contact_device(bem_kernel_s* k, const bem_problem* prob, const 
                                 uint8_t* mask, void* p_out, bem_result* res, cudaStream_t s);
 bem_status solve_batch_device(int n, bem_kernel_s* const* ks, const bem_problem* probs, const bool* has_pinit,
                               bem_result* res, cudaStream_t const* strm);
+void release_batch_graph(const bem_kernel_s* k);
 
 // Argument checks of an operator description (shared with the allocation-free
 // entry point).
@@ -99,6 +100,26 @@ cudaStream_t batch_stream(int dev, int i) {
   }
   return pool[i % kBatchStreams];
 }
+
+}  // namespace
+
+cudaStream_t capture_stream() {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> per_dev;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
+  if (per_dev[dev] == nullptr) cudaStreamCreateWithFlags(&per_dev[dev], cudaStreamNonBlocking);
+  return per_dev[dev];
+}
+
+uint64_t next_serial() {
+  static std::atomic<uint64_t> ctr{0};
+  return ++ctr;
+}
+
+namespace {
 
 struct DeviceGuard {
   int prev = -1;
@@ -250,6 +271,12 @@ static bem_status apply_radix(bem_kernel_s* k, int row_log2, int col_log2, cudaS
     k->graphs.lin_exec = nullptr;
     k->graphs.lin_nodes = 0;
   }
+  if (k->graphs.loop_exec != nullptr) {
+    BEM_CUDA_TRY(cudaGraphExecDestroy(k->graphs.loop_exec));
+    k->graphs.loop_exec = nullptr;
+    k->graphs.loop_nodes = 0;
+  }
+  k->serial = next_serial();
   k->graphs.warm = 0;   // the next chunk runs plainly once (attributes of the new kernels)
   k->graphs.lin_warm = 0;
   return BEM_OK;
@@ -367,6 +394,7 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
   k->desc = *desc;
   k->n_layers = n_layers;
   for (int l = 0; l < n_layers; ++l) k->layers[l] = layers[l];
+  k->serial = next_serial();
   k->N = desc->N;
   k->M = 2 * desc->N;
   k->logN = 0;
@@ -443,6 +471,8 @@ bem_status bem_destroy_kernel(bem_kernel k) {
   harvest_pass_timing(k);
   if (k->graphs.pk_exec != nullptr) cudaGraphExecDestroy(k->graphs.pk_exec);
   if (k->graphs.lin_exec != nullptr) cudaGraphExecDestroy(k->graphs.lin_exec);
+  if (k->graphs.loop_exec != nullptr) cudaGraphExecDestroy(k->graphs.loop_exec);
+  release_batch_graph(k);
   for (auto& e : k->timing.pool) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);

@@ -88,6 +88,8 @@ struct SolveState {
   int replace;       // 1: recompute the gap from u = K p before the next iteration
   int x_clear;       // 1: this iteration consumed x (its correction ran), so the update rewrites x from 0
   int restart_next;  // 1: the last direction was not a descent direction (no step taken): restart
+  int loops;         // bodies of the device-side iteration loop executed
+  int max_loops;     // bound on them (iteration limit / chunk + 2)
 };
 
 // Workspace owned by a kernel handle.
@@ -142,8 +144,13 @@ struct bem_kernel_s {
     cudaGraphExec_t lin_exec = nullptr;
     long long lin_nodes = 0;
     const void* lin_mask = nullptr;    // contact mask the linear chunk was captured with
+    // the whole constrained-CG iteration as one graph: a conditional 'while' node whose
+    // body is one chunk plus the loop control (device-side loop, no host round trip)
+    cudaGraphExec_t loop_exec = nullptr;
+    long long loop_nodes = 0;          // kernel nodes per body execution
   };
   Graphs graphs;
+  uint64_t serial = 0;  // identity of the handle's captured kernels (new on creation and radix change)
 };
 
 namespace bem {
@@ -164,6 +171,10 @@ long long launches();
 // adds the durations of completed timed passes of k to its totals (host sync point)
 void harvest_pass_timing(const bem_kernel_s* k);
 bem_status cuda_fail(cudaError_t e, const char* what);
+// api.cu: a library-owned stream of the current device used only to capture graphs
+cudaStream_t capture_stream();
+// api.cu: a fresh identity for a handle's captured kernels
+uint64_t next_serial();
 // api.cu: BEM_OK when the description is valid, else BEM_EINVAL with a message
 bem_status check_desc(const bem_kernel_desc* d);
 
@@ -180,6 +191,12 @@ template <typename T>
 void reg_pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s, const int* skip);
 template <typename T>
 void reg_twiddles(const bem_kernel_s* k, cudaStream_t s);
+template <typename T>
+void reg_prepare(const bem_kernel_s* k);
+// matvec.cu: sets the one-time kernel attributes of the product's passes for k
+// (what the first plain launch would set), so that a graph capture can follow
+template <typename T>
+void prepare_passes(const bem_kernel_s* k);
 int stage_tw_count(int logl);
 size_t table_bytes(const bem_kernel_s* k);
 

@@ -416,6 +416,14 @@ void launch_pass(const bem_kernel_s* k, int pass, const T* p, T* u, cudaStream_t
   pass_impl<T>(k, pass, p, u, s, nullptr);
 }
 
+template <typename T>
+void prepare_passes(const bem_kernel_s* k) {
+  if (k->logN >= 4) reg_prepare<T>(k);
+  else set_smem_attrs<T>();
+}
+
+template void prepare_passes<float>(const bem_kernel_s*);
+template void prepare_passes<double>(const bem_kernel_s*);
 template void launch_pass<float>(const bem_kernel_s*, int, const float*, float*, cudaStream_t);
 template void launch_pass<double>(const bem_kernel_s*, int, const double*, double*, cudaStream_t);
 template void launch_matvec<float>(const bem_kernel_s*, const float*, float*, cudaStream_t, const int*);

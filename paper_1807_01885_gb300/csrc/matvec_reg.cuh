@@ -212,12 +212,16 @@ __global__ void k_stage_twiddles(cplx<T>* __restrict__ out, int logl, int logr) 
 template <typename T, int LOGN, int LOGR>
 struct RowLaunch {
   using C = cplx<T>;
-  static void pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s, const int* skip) {
+  // one-time per-device kernel attributes (also called before a graph capture)
+  static void prepare() {
     static std::atomic<unsigned long long> attr{0};
     if (first_on_device(attr)) {
       cudaFuncSetAttribute(k_row_fwd_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_row_inv_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }
+  }
+  static void pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s, const int* skip) {
+    prepare();
     constexpr int N = 1 << LOGN;
     using PR = Plan<LOGN, LOGR>;
     constexpr int rpb = rows_per_block<T, LOGN, LOGR>();
@@ -235,10 +239,13 @@ struct RowLaunch {
 template <typename T, int LOGN, int LOGR>
 struct ColLaunch {
   using C = cplx<T>;
-  static void pass(const bem_kernel_s* k, const int* skip, cudaStream_t s) {
+  static void prepare() {
     static std::atomic<unsigned long long> attr{0};
     if (first_on_device(attr))
       cudaFuncSetAttribute(k_col_r<T, LOGN + 1, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
+  static void pass(const bem_kernel_s* k, const int* skip, cudaStream_t s) {
+    prepare();
     constexpr int N = 1 << LOGN;
     using PC = Plan<LOGN + 1, LOGR>;
     constexpr int cpb = cols_per_block<T, LOGN + 1, LOGR>();
@@ -269,6 +276,21 @@ void by_logn(int logn, A... a) {
   }
 }
 
+template <typename T, template <typename, int, int> class L, int LOGR>
+void by_logn_prepare(int logn) {
+  switch (logn) {
+    case 4: L<T, 4, LOGR>::prepare(); break;
+    case 5: L<T, 5, LOGR>::prepare(); break;
+    case 6: L<T, 6, LOGR>::prepare(); break;
+    case 7: L<T, 7, LOGR>::prepare(); break;
+    case 8: L<T, 8, LOGR>::prepare(); break;
+    case 9: L<T, 9, LOGR>::prepare(); break;
+    case 10: L<T, 10, LOGR>::prepare(); break;
+    case 11: L<T, 11, LOGR>::prepare(); break;
+    default: break;
+  }
+}
+
 template <typename T>
 int row_logr(const bem_kernel_s* k) { return k->row_radix_alt ? Radix<T>::ROW_ALT : Radix<T>::ROW; }
 template <typename T>
@@ -283,6 +305,15 @@ void reg_pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s
     if (row_logr<T>(k) == 4) by_logn<T, RowLaunch, 4>(k->logN, k, which, p, u, s, skip);
     else by_logn<T, RowLaunch, 3>(k->logN, k, which, p, u, s, skip);
   }
+}
+
+// kernel attributes of the passes a handle launches, set before a graph capture
+template <typename T>
+void reg_prepare(const bem_kernel_s* k) {
+  if (col_logr<T>(k) == 4) by_logn_prepare<T, ColLaunch, 4>(k->logN);
+  else by_logn_prepare<T, ColLaunch, 3>(k->logN);
+  if (row_logr<T>(k) == 4) by_logn_prepare<T, RowLaunch, 4>(k->logN);
+  else by_logn_prepare<T, RowLaunch, 3>(k->logN);
 }
 
 template <typename T>

@@ -16,6 +16,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 #include <unordered_set>
 #include <vector>
 
@@ -739,6 +740,8 @@ bem_status pk_setup(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cu
   init.max_iter = prob->max_iter;
   init.n_neg = 1;  // no convergence test passes before one full iteration
   init.res_replaced = 1e300;
+  init.loops = 0;
+  init.max_loops = prob->max_iter / CHUNK + 2;
   init.status = BEM_OK;
   init.mv_t_on = 1;
   // products outside the iteration: one for the depth-control initial guess, or the
@@ -837,6 +840,130 @@ bem_status pk_chunk(bem_kernel_s* k, cudaStream_t s) {
   return chunk_graph(k, s, gr.pk_exec, gr.pk_nodes, gr.warm, [&] { pk_chunk_launches<T>(k, s); });
 }
 
+// Loop control of the device-side iteration, the condition of a conditional 'while'
+// node of a CUDA graph: the next body runs while the solve is unfinished.  A solve
+// still running after max_loops bodies stops with BEM_ENOCONV, which bounds the
+// loop whatever the CG kernels do.
+__global__ void k_loop_ctl(SolveState* st, cudaGraphConditionalHandle h) {
+  st->loops += 1;
+  if (!st->done && st->loops >= st->max_loops) finish(st, BEM_ENOCONV);
+  cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+// Solves up to this iteration limit run the device-side loop; longer ones keep the
+// host loop (a state read every chunk), as do traced and pass-timed solves.
+constexpr int kDeviceLoopMaxIter = 200000;
+
+bool device_loop(const bem_kernel_s* k, const bem_problem* prob, bool trace) {
+  return !k->timing.on && !trace && prob->max_iter <= kDeviceLoopMaxIter;
+}
+
+// Adds to graph g a conditional 'while' node whose body is one chunk of k's
+// constrained CG followed by the loop control; the body is captured on the library's
+// capture stream (nothing runs).  *body_nodes: kernel nodes per body execution.
+template <typename T>
+bem_status add_loop_node(bem_kernel_s* k, cudaGraph_t g, long long* body_nodes) {
+  cudaGraphConditionalHandle h;
+  BEM_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  BEM_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = capture_stream();
+  prepare_passes<T>(k);
+  const long long before = launches();
+  BEM_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pk_chunk_launches<T>(k, cs);
+  k_loop_ctl<<<1, 1, 0, cs>>>(k->ws.state, h);
+  note_launches(1);
+  const cudaError_t e = cudaStreamEndCapture(cs, &body);
+  *body_nodes = launches() - before;
+  note_launches(-*body_nodes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (iteration loop)");
+  return BEM_OK;
+}
+
+// The handle's whole-solve loop graph, built once.
+template <typename T>
+bem_status loop_graph(bem_kernel_s* k) {
+  auto& gr = k->graphs;
+  if (gr.loop_exec != nullptr) return BEM_OK;
+  cudaGraph_t g = nullptr;
+  BEM_CUDA_TRY(cudaGraphCreate(&g, 0));
+  long long nodes = 0;
+  bem_status st = add_loop_node<T>(k, g, &nodes);
+  if (st == BEM_OK) {
+    const cudaError_t e = cudaGraphInstantiate(&gr.loop_exec, g, 0);
+    if (e != cudaSuccess) {
+      gr.loop_exec = nullptr;
+      st = cuda_fail(e, "cudaGraphInstantiate (iteration loop)");
+    }
+  }
+  cudaGraphDestroy(g);
+  gr.loop_nodes = nodes;
+  return st;
+}
+
+// Cache of batch graphs: one graph holds a loop node per instance (no edges between
+// them, so the instances run concurrently) and is reused while the same handles, with
+// the same captured kernels, come back in the same order.
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  std::vector<const bem_kernel_s*> ks;
+  std::vector<long long> nodes;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_cache;
+constexpr size_t kBatchCacheSize = 4;
+
+template <typename T>
+bem_status batch_graph(bem_kernel_s* const* ks, const std::vector<int>& idx, cudaGraphExec_t* exec,
+                       std::vector<long long>* nodes) {
+  std::vector<uint64_t> key;
+  for (int i : idx) key.push_back(ks[i]->serial);
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (auto& b : g_batch_cache) {
+    if (b.key == key) {
+      *exec = b.exec;
+      *nodes = b.nodes;
+      return BEM_OK;
+    }
+  }
+  cudaGraph_t g = nullptr;
+  BEM_CUDA_TRY(cudaGraphCreate(&g, 0));
+  BatchGraph b;
+  b.key = key;
+  bem_status st = BEM_OK;
+  for (int i : idx) {
+    long long n = 0;
+    if ((st = add_loop_node<T>(ks[i], g, &n)) != BEM_OK) break;
+    b.ks.push_back(ks[i]);
+    b.nodes.push_back(n);
+  }
+  if (st == BEM_OK) {
+    const cudaError_t e = cudaGraphInstantiate(&b.exec, g, 0);
+    if (e != cudaSuccess) {
+      b.exec = nullptr;
+      st = cuda_fail(e, "cudaGraphInstantiate (batch)");
+    }
+  }
+  cudaGraphDestroy(g);
+  if (st != BEM_OK) return st;
+  if (g_batch_cache.size() >= kBatchCacheSize) {
+    cudaGraphExecDestroy(g_batch_cache.front().exec);
+    g_batch_cache.erase(g_batch_cache.begin());
+  }
+  g_batch_cache.push_back(b);
+  *exec = b.exec;
+  *nodes = b.nodes;
+  return BEM_OK;
+}
+
 // CHUNK iterations of the fixed-area linear CG (adhesive inner solve), gated by the
 // device state like the constrained CG's chunk.
 template <typename T>
@@ -871,6 +998,16 @@ bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cuda
   bem_status e = pk_setup<T>(k, prob, pinit, s);
   if (e != BEM_OK) return e;
   static const bool trace = getenv("BEM_TRACE") != nullptr;   // diagnostic: residual per chunk on stderr
+  if (device_loop(k, prob, trace)) {
+    // the whole iteration in one graph launch; one state read at the end
+    e = loop_graph<T>(k);
+    if (e != BEM_OK) return e;
+    BEM_CUDA_TRY(cudaGraphLaunch(k->graphs.loop_exec, s));
+    e = read_state<T>(k, s);
+    if (e != BEM_OK) return e;
+    note_launches((long long)k->ws.state_host->loops * k->graphs.loop_nodes);
+    return BEM_OK;
+  }
   for (;;) {
     e = pk_chunk<T>(k, s);
     if (e != BEM_OK) return e;
@@ -1072,6 +1209,34 @@ bem_status batch_typed(int n, bem_kernel_s* const* ks, const bem_problem* probs,
     active.push_back(i);
   }
   std::vector<int> next, finished;
+  bool device = !active.empty();
+  for (int i : active) device = device && device_loop(ks[i], &probs[i], false);
+  if (device) {
+    // one graph launch runs every instance's iteration loop on the device
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> nodes;
+    bem_status e = batch_graph<T>(ks, active, &exec, &nodes);
+    if (e != BEM_OK) return e;
+    cudaStream_t s0 = strm[active[0]];
+    for (int i : active) {
+      BEM_CUDA_TRY(cudaEventRecord(ks[i]->ws.done_ev, strm[i]));
+      BEM_CUDA_TRY(cudaStreamWaitEvent(s0, ks[i]->ws.done_ev, 0));
+    }
+    BEM_CUDA_TRY(cudaGraphLaunch(exec, s0));
+    BEM_CUDA_TRY(cudaEventRecord(ks[active[0]]->ws.done_ev, s0));
+    for (int i : active) {
+      if (strm[i] != s0) BEM_CUDA_TRY(cudaStreamWaitEvent(strm[i], ks[active[0]]->ws.done_ev, 0));
+      BEM_CUDA_TRY(cudaMemcpyAsync(ks[i]->ws.state_host, ks[i]->ws.state, sizeof(SolveState),
+                                   cudaMemcpyDeviceToHost, strm[i]));
+    }
+    for (int i : active) BEM_CUDA_TRY(cudaStreamSynchronize(strm[i]));
+    for (size_t a = 0; a < active.size(); ++a) {
+      const int i = active[a];
+      note_launches((long long)ks[i]->ws.state_host->loops * nodes[a]);
+      finished.push_back(i);
+    }
+    active.clear();
+  }
   while (!active.empty()) {
     for (int i : active) {
       bem_kernel_s* k = ks[i];
@@ -1109,6 +1274,19 @@ bem_status batch_typed(int n, bem_kernel_s* const* ks, const bem_problem* probs,
 }
 
 }  // namespace
+
+void release_batch_graph(const bem_kernel_s* k) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (size_t b = 0; b < g_batch_cache.size();) {
+    auto& ks = g_batch_cache[b].ks;
+    if (std::find(ks.begin(), ks.end(), k) != ks.end()) {
+      cudaGraphExecDestroy(g_batch_cache[b].exec);
+      g_batch_cache.erase(g_batch_cache.begin() + b);
+    } else {
+      ++b;
+    }
+  }
+}
 
 bem_status solve_batch_device(int n, bem_kernel_s* const* ks, const bem_problem* probs, const bool* has_pinit,
                               bem_result* res, cudaStream_t const* strm) {

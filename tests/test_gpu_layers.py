@@ -53,7 +53,13 @@ def test_one_layer_stack_equals_single_coating(cuda):
                 a = k.table().cpu().numpy()
             with bem.Kernel(N, delta, layers=[(h, E1, nu1)], E2=E2, nu2=nu2, dc_mode=dc_mode) as k:
                 b = k.table().cpu().numpy()
+            # k != 0: the same formula evaluated two ways, to rounding
+            a0, b0 = a[0, 0], b[0, 0]
+            a[0, 0] = b[0, 0] = 1.0
             np.testing.assert_allclose(b, a, rtol=1e-13, atol=0)
+            # k = 0: the closed-form finite part of Eq. (9) against the dual-number
+            # derivative through the stack's solve (cancellation leaves ~1e-13)
+            assert b0 == pytest.approx(a0, rel=1e-12, abs=1e-15 * abs(a).max())
 
 
 def test_stack_table_large_grid_samples(cuda):

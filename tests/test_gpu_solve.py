@@ -303,3 +303,34 @@ def test_full_size_fp32_solve_satisfies_contact_conditions(cuda):
     assert abs(float(g[C].mean())) < 1e-6 * scale
     assert float(g[~C].min()) > -1e-6 * scale        # no penetration outside the contact set
     assert res["err_est"] < 1e-6
+
+
+@pytest.mark.parametrize("control", ["force", "depth"])
+def test_device_loop_equals_host_loop(cuda, control):
+    """A solve runs its whole iteration as one graph launch (a conditional 'while' node
+    over chunks of CG iterations, stopped by the device state).  With pass timing on the
+    library runs the same kernels as plain launches from a host loop that reads the
+    state every chunk; both give the same pressure bit for bit, the same iteration and
+    product counts, and the iteration limit stops both alike."""
+    inst = inputs.batch_instance(20260300, sizes=(256,))
+    with bem.Kernel(256, inst["delta"], inst["h"], inst["E1"], inst["nu1"], inst["E2"], inst["nu2"],
+                    precision="fp32") as k:
+        ht = torch.tensor(inst["height"], device=cuda, dtype=torch.float32)
+        target = inst["force"] if control == "force" else float(ht.max()) * 0.002
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            p_dev, r_dev = k.solve(ht, control, target, tol=1e-8, stream=s)
+            p_dev = p_dev.clone()
+            bem.bem_set_pass_timing(k.handle, True)
+            p_host, r_host = k.solve(ht, control, target, tol=1e-8, stream=s)
+            bem.bem_set_pass_timing(k.handle, False)
+            # the iteration limit ends the device loop with BEM_ENOCONV
+            n0 = bem.bem_launch_count()
+            _, r_lim = k.solve(ht, control, target, tol=1e-8, max_iter=5, stream=s)
+            n1 = bem.bem_launch_count()
+        s.synchronize()
+    assert r_dev["status"] == 0 and r_host["status"] == 0
+    assert torch.equal(p_dev, p_host)
+    assert r_dev["iters"] == r_host["iters"] and r_dev["matvecs"] == r_host["matvecs"]
+    assert r_lim["status"] == bem.BEM_ENOCONV and r_lim["iters"] == 5
+    assert n1 > n0

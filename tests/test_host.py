@@ -135,9 +135,18 @@ def test_alg_bytes_counts_stored_arrays(bench):
 
 
 def test_profiled_traffic_gated_on_sources(bench, tmp_path, monkeypatch):
-    text = open(bench.PROFILE).read()
-    val = bench.profiled_traffic()
-    assert val is not None and f"traffic_bytes_per_launch: {val}" in text
+    """The ncu traffic figure is used only while the profiled sources hash to the value
+    recorded beside it: a summary written for the current sources gives its figure,
+    any other hash (a kernel edit since the capture) gives None."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in bench.PROFILED_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    text = f"notes\n\n    traffic_bytes_per_launch: 12345\n    source_sha256: {h.hexdigest()}\n"
+    cur = tmp_path / "cur.md"
+    cur.write_text(text)
+    monkeypatch.setattr(bench, "PROFILE", str(cur))
+    assert bench.profiled_traffic() == 12345
     # a different source hash (any kernel edit since the capture) voids the figure
     bad = tmp_path / "p.md"
     bad.write_text(text.replace("source_sha256: ", "source_sha256: 0"))
@@ -149,13 +158,20 @@ def test_profiled_traffic_gated_on_sources(bench, tmp_path, monkeypatch):
 
 def test_profiled_traffic_tracks_a_source_edit(bench, tmp_path, monkeypatch):
     """Copies of the profiled sources with one byte appended no longer match."""
+    import hashlib
     root = tmp_path / "r"
+    h = hashlib.sha256()
     for f in bench.PROFILED_SOURCES:
         dst = root / f
         dst.parent.mkdir(parents=True, exist_ok=True)
-        dst.write_bytes(open(os.path.join(ROOT, f), "rb").read())
+        data = open(os.path.join(ROOT, f), "rb").read()
+        dst.write_bytes(data)
+        h.update(data)
+    prof = tmp_path / "prof.md"
+    prof.write_text(f"    traffic_bytes_per_launch: 777\n    source_sha256: {h.hexdigest()}\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.profiled_traffic() is not None
+    monkeypatch.setattr(bench, "PROFILE", str(prof))
+    assert bench.profiled_traffic() == 777
     with open(root / bench.PROFILED_SOURCES[0], "ab") as fh:
         fh.write(b"\n")
     assert bench.profiled_traffic() is None
