@@ -326,6 +326,10 @@ def batch_bench(torch, dev, bem, inputs, n_inst, radix):
         st, res = bem.bem_solve_batch(handles, probs, outs, stream=s)
         s.synchronize()
         t_batch = time.perf_counter() - t0
+        # warm-up of the one-after-another path (each handle's own loop graph)
+        for k, pr, o in zip(ks, probs, outs):
+            bem.bem_solve_contact(k.handle, pr, o, stream=s)
+        s.synchronize()
         t0 = time.perf_counter()
         seq = [bem.bem_solve_contact(k.handle, pr, o, stream=s) for k, pr, o in zip(ks, probs, outs)]
         s.synchronize()

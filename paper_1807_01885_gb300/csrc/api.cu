@@ -142,6 +142,7 @@ void free_ws(bem_kernel_s* k) {
   cudaFree(w.tw);
   cudaFree(w.twr);
   cudaFree(w.twc);
+  cudaFree(w.twpc);
   cudaFree(w.vec);
   cudaFree(w.mask);
   cudaFree(w.partials);
@@ -424,6 +425,9 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
     return fail(e, "cudaMalloc(twr)");
   if ((e = cudaMalloc(&w.twc, (size_t)stage_tw_count(k->logN + 1) * 2 * k->elem)) != cudaSuccess)
     return fail(e, "cudaMalloc(twc)");
+  if (k->prec == BEM_FP32 &&
+      (e = cudaMalloc(&w.twpc, (size_t)pair_tw_count(k->logN + 1) * 4 * sizeof(float))) != cudaSuccess)
+    return fail(e, "cudaMalloc(twpc)");
   if ((e = cudaMalloc(&w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
   if ((e = cudaMalloc((void**)&w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
   if ((e = cudaMalloc((void**)&w.partials, 16 * 2048 * sizeof(double))) != cudaSuccess)

@@ -100,6 +100,7 @@ struct Workspace {
   void* tw = nullptr;        // M complex: e^{-2 pi i k / M}
   void* twr = nullptr;       // stage twiddles of the length-N register FFT (rows)
   void* twc = nullptr;       // stage twiddles of the length-2N register FFT (columns)
+  void* twpc = nullptr;      // float path: broadcast stage twiddles of the paired column FFT (4N float4)
   void* vec = nullptr;       // solver vectors: p, g, t, r, u, f, x (N*N each)
   uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy; PK: contact set {p > 0}
   double* partials = nullptr;// per-block partial sums
@@ -198,6 +199,8 @@ void reg_prepare(const bem_kernel_s* k);
 template <typename T>
 void prepare_passes(const bem_kernel_s* k);
 int stage_tw_count(int logl);
+// float4 records of the paired FFT's stage twiddles for length 2^logl (upper bound)
+int pair_tw_count(int logl);
 size_t table_bytes(const bem_kernel_s* k);
 
 // solve.cu

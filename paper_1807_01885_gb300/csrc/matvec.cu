@@ -119,6 +119,20 @@ __global__ void k_table_square(const double* __restrict__ t64, T* __restrict__ t
   }
 }
 
+// Float register path: the compliance in column pairs, scaled by 1/M^2:
+// tab2[p (N + 1) + f] = (K(f, 2p), K(f, 2p + 1)), p in [0, N/2], f in [0, N]; the
+// column N + 1 of the last pair does not exist and holds 0.
+__global__ void k_table_pair(const double* __restrict__ t64, float2* __restrict__ tab, int N, double scale) {
+  const size_t total = (size_t)(N / 2 + 1) * (N + 1);
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / (N + 1), f = idx % (N + 1);
+    const size_t ja = 2 * p, jb = 2 * p + 1;
+    const float a = (float)(t64[f * (N + 1) + ja] * scale);
+    const float b = jb <= (size_t)N ? (float)(t64[f * (N + 1) + jb] * scale) : 0.f;
+    tab[idx] = make_float2(a, b);
+  }
+}
+
 template <typename T>
 __global__ void k_twiddles(cplx<T>* __restrict__ tw, int M) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
@@ -152,6 +166,9 @@ static void layered_constants(const bem_kernel_desc& d, double* A, double* B, do
 // Upper bound on the stage twiddle entries of a length-2^logl register FFT: the
 // stage tables hold sum_{s>=1} R_s Ns_s = sum_{s>=1} Ns_{s+1} < 2L values.
 int stage_tw_count(int logl) { return 2 << logl; }
+// the paired tables hold at most Q planes of Ns records per stage (twp_planes(Q) <= Q
+// for every radix used), and sum_{s>=1} Q_s Ns_s < 2L as above
+int pair_tw_count(int logl) { return 2 << logl; }
 
 size_t spec_bytes(const bem_kernel_s* k) {
   return (size_t)(k->N / TC + 1) * k->N * TC * 2 * k->elem;
@@ -204,7 +221,7 @@ bem_status build_table(bem_kernel_s* k, cudaStream_t s) {
     k_twiddles<double><<<(k->M + 255) / 256, 256, 0, s>>>((double2*)k->ws.tw, k->M);
     if (k->logN >= 4) reg_twiddles<double>(k, s);
   } else {
-    if (k->logN >= 4) k_table_square<float><<<256, 256, 0, s>>>(k->ws.table64, (float*)k->ws.table, k->N, scale);
+    if (k->logN >= 4) k_table_pair<<<256, 256, 0, s>>>(k->ws.table64, (float2*)k->ws.table, k->N, scale);
     else k_table_block<float><<<256, 256, 0, s>>>(k->ws.table64, (float*)k->ws.table, k->N, scale);
     k_twiddles<float><<<(k->M + 255) / 256, 256, 0, s>>>((float2*)k->ws.tw, k->M);
     if (k->logN >= 4) reg_twiddles<float>(k, s);

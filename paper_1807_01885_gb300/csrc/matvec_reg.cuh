@@ -15,6 +15,7 @@
 #pragma once
 
 #include "bem_internal.cuh"
+#include "fft_pair.cuh"
 #include "fft_reg.cuh"
 
 namespace bem {
@@ -43,6 +44,14 @@ __device__ __forceinline__ void cp_async_elem(C* smem, const C* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// complex slots of one row's shared buffer in the row passes: the padded exchange
+// buffer plus 8, rounded up to an even count so that every row's buffer starts on a
+// 16-byte boundary (the float inverse pass copies 16-byte records into it)
+template <int LOGN, int LOGR>
+__host__ __device__ constexpr int row_sh() {
+  return Plan<LOGN, LOGR>::PADL + 8 + (Plan<LOGN, LOGR>::PADL & 1);
+}
+
 // rows per block of the row passes and columns per block of the column pass
 template <typename T, int LOGN, int LOGR>
 __host__ __device__ constexpr int rows_per_block() {
@@ -61,7 +70,7 @@ k_row_fwd_r(const T* __restrict__ p, cplx<T>* __restrict__ spec, const cplx<T>* 
             const cplx<T>* __restrict__ tw, const int* __restrict__ skip) {
   using C = cplx<T>;
   using P = Plan<LOGN, LOGR>;
-  constexpr int N = 1 << LOGN, TT = P::T, SH = P::PADL + 8, R = P::R;
+  constexpr int N = 1 << LOGN, TT = P::T, SH = row_sh<LOGN, LOGR>(), R = P::R;
   constexpr int RPB = rows_per_block<T, LOGN, LOGR>();
   if (skip != nullptr && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -79,26 +88,56 @@ k_row_fwd_r(const T* __restrict__ p, cplx<T>* __restrict__ spec, const cplx<T>* 
 #pragma unroll
   for (int q = 0; q < R; ++q) sh[padi<LOGR>(t + TT * q)] = v[q];
   __syncthreads();
-  // Recombination and column-major store: thread (j0, rr) = (tid / RPB, tid mod RPB)
-  // forms X[j] of row r0 + rr for j = j0 + TT k, k = 0..R (k = R: only j = N), so
-  // that the RPB rows of one frequency, contiguous in spec, go out in one sector.
   const int j0 = threadIdx.x / RPB, rr = threadIdx.x - j0 * RPB;
   const C* shr = sh0 + rr * SH;
-  C* out = spec + r0 + rr;
-  const C wt = sizeof(T) == 4 ? tw[j0] : mk((T)0, (T)0);
+  if constexpr (sizeof(T) == 4) {
+    // Float: the spectrum is stored in column pairs (spec4[jp N + r] holds the re and
+    // im of frequencies 2jp and 2jp + 1 of row r as (re_2jp, re_2jp+1, im_2jp,
+    // im_2jp+1)), the layout the paired column pass reads.  Thread (j0, rr) forms X[j]
+    // and X[j + 1] of row r0 + rr for j = 2 (j0 + TT k / 2), k = 0, 2, .., R - 2, so
+    // that the RPB rows of one frequency pair go out as one 16-byte store each.
+    float4* out4 = reinterpret_cast<float4*>(spec) + r0 + rr;
+    const C wa = tw[2 * j0], wb = tw[2 * j0 + 1];
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int j = j0 + TT * k;
-    const C za = shr[padi<LOGR>(j)];
-    const C zb = cconj(shr[padi<LOGR>((N - j) & (N - 1))]);
-    const C E = cscale(cadd(za, zb), (T)0.5);
-    const C O = cscale(cmul_mi(csub(za, zb)), (T)0.5);
-    out[(size_t)j * N] = cadd(E, cmul(O, recomb_tw<T, R>(tw, wt, j, k)));
-  }
-  if (j0 == 0) {
-    // j = N (Nyquist): X[N] = Re Z[0] - Im Z[0]
-    const C z0 = shr[0];
-    out[(size_t)N * N] = mk(z0.x - z0.y, (T)0);
+    for (int k = 0; k < R; k += 2) {
+      const int j = 2 * j0 + TT * k;   // TT k = N k / R: the frequencies 2 j0 + (N/R) k and + 1
+      C X2[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int jj = j + e;
+        const C za = shr[padi<LOGR>(jj)];
+        const C zb = cconj(shr[padi<LOGR>((N - jj) & (N - 1))]);
+        const C E = cscale(cadd(za, zb), (T)0.5);
+        const C O = cscale(cmul_mi(csub(za, zb)), (T)0.5);
+        X2[e] = cadd(E, cmul(O, recomb_tw<T, R>(tw, e ? wb : wa, jj, k)));
+      }
+      out4[(size_t)(j / 2) * N] = make_float4(X2[0].x, X2[1].x, X2[0].y, X2[1].y);
+    }
+    if (j0 == 0) {
+      // pair N/2: j = N (Nyquist, X[N] = Re Z[0] - Im Z[0]) and an empty column N + 1
+      const C z0 = shr[0];
+      out4[(size_t)(N / 2) * N] = make_float4(z0.x - z0.y, 0.f, 0.f, 0.f);
+    }
+  } else {
+    // Recombination and column-major store: thread (j0, rr) = (tid / RPB, tid mod RPB)
+    // forms X[j] of row r0 + rr for j = j0 + TT k, k = 0..R (k = R: only j = N), so
+    // that the RPB rows of one frequency, contiguous in spec, go out in one sector.
+    C* out = spec + r0 + rr;
+    const C wt = mk((T)0, (T)0);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int j = j0 + TT * k;
+      const C za = shr[padi<LOGR>(j)];
+      const C zb = cconj(shr[padi<LOGR>((N - j) & (N - 1))]);
+      const C E = cscale(cadd(za, zb), (T)0.5);
+      const C O = cscale(cmul_mi(csub(za, zb)), (T)0.5);
+      out[(size_t)j * N] = cadd(E, cmul(O, recomb_tw<T, R>(tw, wt, j, k)));
+    }
+    if (j0 == 0) {
+      // j = N (Nyquist): X[N] = Re Z[0] - Im Z[0]
+      const C z0 = shr[0];
+      out[(size_t)N * N] = mk(z0.x - z0.y, (T)0);
+    }
   }
 }
 
@@ -108,7 +147,7 @@ k_row_inv_r(const cplx<T>* __restrict__ spec, T* __restrict__ u, const cplx<T>* 
             const cplx<T>* __restrict__ tw, const int* __restrict__ skip) {
   using C = cplx<T>;
   using P = Plan<LOGN, LOGR>;
-  constexpr int N = 1 << LOGN, TT = P::T, SH = P::PADL + 8, R = P::R;
+  constexpr int N = 1 << LOGN, TT = P::T, SH = row_sh<LOGN, LOGR>(), R = P::R;
   constexpr int RPB = rows_per_block<T, LOGN, LOGR>(), NT = RPB * TT;
   if (skip != nullptr && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -116,29 +155,59 @@ k_row_inv_r(const cplx<T>* __restrict__ spec, T* __restrict__ u, const cplx<T>* 
   const int rl = threadIdx.x / TT, t = threadIdx.x - rl * TT;
   const int r0 = blockIdx.x * RPB;
   C* sh = sh0 + rl * SH;
-  // column-major load of the RPB rows' half spectra Y[j], j in [0, N], copied
-  // asynchronously from global to shared memory (no register staging)
-  const C* in = spec + r0;
-#pragma unroll
-  for (int k = 0; k < (RPB * (N + 1) + NT - 1) / NT; ++k) {
-    const int e = threadIdx.x + NT * k;
-    if (e < RPB * (N + 1)) {
-      const int j = e / RPB, rr = e - j * RPB;
-      cp_async_elem(sh0 + rr * SH + j, in + (size_t)j * N + rr);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
   C v[R];
-  const C wt = sizeof(T) == 4 ? tw[t] : mk((T)0, (T)0);
+  if constexpr (sizeof(T) == 4) {
+    // float: the RPB rows' frequency pairs (spec4[jp N + r], jp in [0, N/2], the
+    // layout of the paired column pass) copied asynchronously as 16-byte records into
+    // each row's buffer, record jp at float offset 4 jp: Y[j] = (buf[4 (j/2) + j%2],
+    // buf[4 (j/2) + 2 + j%2])
+    const float4* in4 = reinterpret_cast<const float4*>(spec) + r0;
+    constexpr int NP = N / 2 + 1;
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int j = t + TT * q;
-    const C y1 = sh[j];
-    const C y2 = cconj(sh[N - j]);
-    const C e = cadd(y1, y2);
-    const C o = cmul_pi(cmulc(csub(y1, y2), recomb_tw<T, R>(tw, wt, j, q)));
-    v[q] = cadd(e, o);
+    for (int k = 0; k < (RPB * NP + NT - 1) / NT; ++k) {
+      const int e = threadIdx.x + NT * k;
+      if (e < RPB * NP) {
+        const int jp = e / RPB, rr = e - jp * RPB;
+        cp_async_elem(reinterpret_cast<float4*>(sh0 + rr * SH) + jp, in4 + (size_t)jp * N + rr);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const float* buf = reinterpret_cast<const float*>(sh);
+    const C wt = tw[t];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int j = t + TT * q, jr = N - j;
+      const C y1 = mk(buf[4 * (j >> 1) + (j & 1)], buf[4 * (j >> 1) + 2 + (j & 1)]);
+      const C y2 = mk(buf[4 * (jr >> 1) + (jr & 1)], -buf[4 * (jr >> 1) + 2 + (jr & 1)]);
+      const C e = cadd(y1, y2);
+      const C o = cmul_pi(cmulc(csub(y1, y2), recomb_tw<T, R>(tw, wt, j, q)));
+      v[q] = cadd(e, o);
+    }
+  } else {
+    // column-major load of the RPB rows' half spectra Y[j], j in [0, N], copied
+    // asynchronously from global to shared memory (no register staging)
+    const C* in = spec + r0;
+#pragma unroll
+    for (int k = 0; k < (RPB * (N + 1) + NT - 1) / NT; ++k) {
+      const int e = threadIdx.x + NT * k;
+      if (e < RPB * (N + 1)) {
+        const int j = e / RPB, rr = e - j * RPB;
+        cp_async_elem(sh0 + rr * SH + j, in + (size_t)j * N + rr);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const C wt = mk((T)0, (T)0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int j = t + TT * q;
+      const C y1 = sh[j];
+      const C y2 = cconj(sh[N - j]);
+      const C e = cadd(y1, y2);
+      const C o = cmul_pi(cmulc(csub(y1, y2), recomb_tw<T, R>(tw, wt, j, q)));
+      v[q] = cadd(e, o);
+    }
   }
   __syncthreads();
   reg_fft<LOGN, LOGR, true, false, T, RPB>(v, sh, twr, t, rl);
@@ -180,6 +249,81 @@ k_col_r(cplx<T>* __restrict__ spec, const T* __restrict__ table, const cplx<T>* 
   if (active) {
 #pragma unroll
     for (int q = 0; q < R / 2; ++q) col[t + TT * q] = v[q];
+  }
+}
+
+// Float column pass on column pairs: block c-slot handles the frequency columns 2 pr
+// and 2 pr + 1 (pr < npairs = N/2 + 1; the second column of the last pair is the
+// empty column N + 1, whose compliance is 0) as one packed transform (fft_pair.cuh):
+// the length-2N FFT of the N nonzero rows (first stage pruned), times the pair of
+// compliances (tab2[pr (N + 1) + f] = (K(f, 2 pr), K(f, 2 pr + 1)) / M^2, f the folded
+// row wave number), the inverse FFT, the first N rows kept.
+template <int LOGR> struct ColPairCfg { static constexpr int MAXT = 256, MINB = 2; };
+template <> struct ColPairCfg<3> { static constexpr int MAXT = 512, MINB = 1; };
+
+template <int LOGM, int LOGR>
+__host__ __device__ constexpr int pairs_per_block() {
+  constexpr int c = ColPairCfg<LOGR>::MAXT / Plan<LOGM, LOGR>::T;
+  return c < 1 ? 1 : c;
+}
+
+template <int LOGM, int LOGR>
+__global__ void __launch_bounds__(ColPairCfg<LOGR>::MAXT, ColPairCfg<LOGR>::MINB)
+k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float4* __restrict__ twp, int npairs,
+        const int* __restrict__ skip) {
+  using P = Plan<LOGM, LOGR>;
+  using pr::CP;
+  constexpr int M = 1 << LOGM, N = M / 2, TT = P::T, SH = P::PADL + 8, R = P::R;
+  constexpr int CPB = pairs_per_block<LOGM, LOGR>();
+  if (skip != nullptr && *skip == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = threadIdx.x / TT, t = threadIdx.x - c * TT;
+  const int pair = blockIdx.x * CPB + c;
+  const bool active = pair < npairs;
+  CP* sh = reinterpret_cast<CP*>(smem_raw) + c * SH;
+  float4* col = spec4 + (size_t)pair * N;
+  CP v[R];
+#pragma unroll
+  for (int q = 0; q < R / 2; ++q) v[q] = active ? pr::cp_load(col + t + TT * q) : pr::cp_zero();
+#pragma unroll
+  for (int q = R / 2; q < R; ++q) v[q] = pr::cp_zero();
+  pr::pair_fft<LOGM, LOGR, false, true, CPB>(v, sh, twp, t, c);
+  const float2* kt = tab2 + (size_t)pair * (N + 1);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = t + TT * q;
+    const int f = (q < R / 2) ? i : M - i;
+    const float2 kv = active ? kt[f] : make_float2(0.f, 0.f);
+    v[q] = pr::cscale2(v[q], pr::pk2(kv.x, kv.y));
+  }
+  pr::pair_fft<LOGM, LOGR, true, false, CPB>(v, sh, twp, t, c);
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) pr::cp_store(col + t + TT * q, v[q]);
+  }
+}
+
+// stage twiddles of the paired FFT (fft_pair.cuh) of length 2^logl, radix 2^logr:
+// stage s >= 1 (radix Q, span Ns) holds, in plane p and record k, the broadcast
+// (wr, wr, wi, wi) of w = e^{-2 pi i k e / (Ns Q)}, e = twp_exponent(Q, p)
+static __global__ void k_stage_twiddles_pair(float4* __restrict__ out, int logl, int logr) {
+  const int sr = logl / logr, logrl = logl % logr;
+  const int nst = sr + (logrl ? 1 : 0);
+  int off = 0, ns = 1;
+  for (int s = 0; s < nst; ++s) {
+    const int Q = (s < sr) ? (1 << logr) : (1 << logrl);
+    if (s > 0) {
+      const int cnt = pr::twp_planes(Q) * ns;
+      for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < cnt; idx += gridDim.x * blockDim.x) {
+        const int k = idx % ns, plane = idx / ns;
+        const int e = pr::twp_exponent(Q, plane);
+        double sn = 0.0, cs = 1.0;
+        sincospi(2.0 * (double)k * (double)e / (double)(ns * Q), &sn, &cs);
+        out[off + idx] = make_float4((float)cs, (float)cs, (float)(-sn), (float)(-sn));
+      }
+      off += cnt;
+    }
+    ns *= Q;
   }
 }
 
@@ -225,7 +369,7 @@ struct RowLaunch {
     constexpr int N = 1 << LOGN;
     using PR = Plan<LOGN, LOGR>;
     constexpr int rpb = rows_per_block<T, LOGN, LOGR>();
-    const size_t smem = (size_t)rpb * (PR::PADL + 8) * sizeof(C);
+    const size_t smem = (size_t)rpb * row_sh<LOGN, LOGR>() * sizeof(C);
     C* spec = (C*)k->ws.spec;
     if (which == 0)
       k_row_fwd_r<T, LOGN, LOGR><<<N / rpb, rpb * PR::T, smem, s>>>(p, spec, (const C*)k->ws.twr,
@@ -241,19 +385,32 @@ struct ColLaunch {
   using C = cplx<T>;
   static void prepare() {
     static std::atomic<unsigned long long> attr{0};
-    if (first_on_device(attr))
-      cudaFuncSetAttribute(k_col_r<T, LOGN + 1, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (first_on_device(attr)) {
+      if constexpr (sizeof(T) == 4)
+        cudaFuncSetAttribute(k_col_p<LOGN + 1, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      else
+        cudaFuncSetAttribute(k_col_r<T, LOGN + 1, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
   }
   static void pass(const bem_kernel_s* k, const int* skip, cudaStream_t s) {
     prepare();
     constexpr int N = 1 << LOGN;
     using PC = Plan<LOGN + 1, LOGR>;
-    constexpr int cpb = cols_per_block<T, LOGN + 1, LOGR>();
-    const int nslots = N + 1;
-    const int grid = (nslots + cpb - 1) / cpb;
-    const size_t smem = (size_t)cpb * (PC::PADL + 8) * sizeof(C);
-    k_col_r<T, LOGN + 1, LOGR><<<grid, cpb * PC::T, smem, s>>>((C*)k->ws.spec, (const T*)k->ws.table,
-                                                             (const C*)k->ws.twc, nslots, skip);
+    if constexpr (sizeof(T) == 4) {
+      constexpr int ppb = pairs_per_block<LOGN + 1, LOGR>();
+      const int npairs = N / 2 + 1;
+      const int grid = (npairs + ppb - 1) / ppb;
+      const size_t smem = (size_t)ppb * (PC::PADL + 8) * sizeof(pr::CP);
+      k_col_p<LOGN + 1, LOGR><<<grid, ppb * PC::T, smem, s>>>((float4*)k->ws.spec, (const float2*)k->ws.table,
+                                                             (const float4*)k->ws.twpc, npairs, skip);
+    } else {
+      constexpr int cpb = cols_per_block<T, LOGN + 1, LOGR>();
+      const int nslots = N + 1;
+      const int grid = (nslots + cpb - 1) / cpb;
+      const size_t smem = (size_t)cpb * (PC::PADL + 8) * sizeof(C);
+      k_col_r<T, LOGN + 1, LOGR><<<grid, cpb * PC::T, smem, s>>>((C*)k->ws.spec, (const T*)k->ws.table,
+                                                               (const C*)k->ws.twc, nslots, skip);
+    }
   }
 };
 
@@ -319,7 +476,10 @@ void reg_prepare(const bem_kernel_s* k) {
 template <typename T>
 void reg_twiddles(const bem_kernel_s* k, cudaStream_t s) {
   k_stage_twiddles<T><<<64, 256, 0, s>>>((cplx<T>*)k->ws.twr, k->logN, row_logr<T>(k));
-  k_stage_twiddles<T><<<64, 256, 0, s>>>((cplx<T>*)k->ws.twc, k->logN + 1, col_logr<T>(k));
+  if constexpr (sizeof(T) == 4)
+    k_stage_twiddles_pair<<<64, 256, 0, s>>>((float4*)k->ws.twpc, k->logN + 1, col_logr<T>(k));
+  else
+    k_stage_twiddles<T><<<64, 256, 0, s>>>((cplx<T>*)k->ws.twc, k->logN + 1, col_logr<T>(k));
 }
 
 }  // namespace bem
