@@ -254,7 +254,7 @@ def bem_matvec_static(N, delta, h, E1, nu1, E2, nu2, p, u, dc_mode=BEM_DC_FINITE
         size = x.numel() if hasattr(x, "numel") else x.size
         if size != N * N:
             raise ValueError(f"bem_matvec_static: {name} must hold N*N = {N * N} values, got {size}")
-        if hasattr(x, "device") and x.device.type == "cuda":
+        if getattr(x, "is_cuda", False):      # a torch tensor on a GPU
             import torch
             if x.device.index != torch.cuda.current_device():
                 raise ValueError(f"bem_matvec_static: {name} is on {x.device}, the current device is "
