@@ -101,6 +101,8 @@ struct Workspace {
   void* twr = nullptr;       // stage twiddles of the length-N register FFT (rows)
   void* twc = nullptr;       // stage twiddles of the length-2N register FFT (columns)
   void* twpc = nullptr;      // float path: broadcast stage twiddles of the paired column FFT (4N float4)
+  void* twpr = nullptr;      // float path: the same for the paired row FFT (2N float4)
+  void* rb4 = nullptr;       // float path: broadcast e^{-i pi j/N}, j in [0, N] (N + 1 float4)
   void* vec = nullptr;       // solver vectors: p, g, t, r, u, f, x (N*N each)
   uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy; PK: contact set {p > 0}
   double* partials = nullptr;// per-block partial sums
