@@ -13,11 +13,14 @@
 // a small last stage, one shared-memory exchange between stages); only the element
 // type and the twiddle form differ.  Twiddles are shared by A and B (same index):
 // they are kept "broadcast", w -> (wr, wr), (wi, wi), (-wi, -wi), so that a product
-// with a CP takes four packed instructions and no register shuffling.  The stage
-// tables store, per k, the broadcast (wr, wr, wi, wi) of the exponents
+// with a CP takes four packed instructions and no register shuffling.  A packed
+// instruction still occupies the FMA pipe for two cycles, so the arithmetic that is
+// the same for both columns (products of twiddles, sign flips) stays scalar or moves
+// to the integer pipe.  The stage tables store, per k, the broadcast
+// (wr, wr, wi, wi) of the exponents
 // Q = 16: 1, 2, 3, 4, 8, 12;  Q = 8: 1, 2, 3, 4;  Q = 4: 1, 2, 3;  Q = 2: 1
 // in planes [plane][k] (one 16-byte load each, consecutive k in consecutive threads);
-// the other exponents are products of two stored ones, formed in packed arithmetic.
+// the other exponents are products of two stored ones, formed in scalar arithmetic.
 #pragma once
 
 #include "fft_reg.cuh"
@@ -80,18 +83,29 @@ __device__ __forceinline__ CP csub(CP a, CP b) { return CP{sub2(a.re, b.re), sub
 // multiply both columns by a real pair (s_A, s_B)
 __device__ __forceinline__ CP cscale2(CP a, f2x s) { return CP{mul2(a.re, s), mul2(a.im, s)}; }
 
-// broadcast twiddle (wr, wr), (wi, wi), (-wi, -wi)
+// sign flip of both halves on the integer pipe (the FMA pipe is the busy one)
+__device__ __forceinline__ f2x neg2(f2x a) {
+  f2x d;
+  asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(d) : "l"(a));
+  return d;
+}
+__device__ __forceinline__ float negf(float a) { return __int_as_float(__float_as_int(a) ^ 0x80000000); }
+
+// broadcast twiddle (wr, wr), (wi, wi), (-wi, -wi), and its scalar value w
 struct TW {
   f2x r, i, ni;
+  float2 w;
 };
 __device__ __forceinline__ TW tw_load(const float4* p) {
   const float4 v = *p;   // (wr, wr, wi, wi)
   const f2x i = pk2(v.z, v.w);
-  return TW{pk2(v.x, v.y), i, sub2(0ull, i)};
+  return TW{pk2(v.x, v.y), i, neg2(i), make_float2(v.x, v.z)};
 }
-// product of two twiddles, in broadcast form
+// product of two twiddles: one scalar complex product (the value is the same for
+// both columns) broadcast by register moves
 __device__ __forceinline__ TW tw_prod(const TW& a, const TW& b) {
-  return TW{fma2(a.i, b.ni, mul2(a.r, b.r)), fma2(a.i, b.r, mul2(a.r, b.i)), fma2(a.ni, b.r, mul2(a.r, b.ni))};
+  const float2 c = make_float2(a.w.x * b.w.x - a.w.y * b.w.y, a.w.x * b.w.y + a.w.y * b.w.x);
+  return TW{pk2(c.x, c.x), pk2(c.y, c.y), pk2(negf(c.y), negf(c.y)), c};
 }
 // x * w (forward) or x * conj(w) (inverse)
 template <bool INV>
@@ -103,10 +117,10 @@ __device__ __forceinline__ CP twmul(CP x, const TW& w) {
 // constant pairs
 __device__ __forceinline__ f2x cpair(float c) { return pk2(c, c); }
 
-// multiply by -+i (INV: +i); costs one packed negation
+// multiply by -+i (INV: +i); the negation is a sign flip on the integer pipe
 template <bool INV>
 __device__ __forceinline__ CP rot4(CP a) {
-  return INV ? CP{sub2(0ull, a.im), a.re} : CP{a.im, sub2(0ull, a.re)};
+  return INV ? CP{neg2(a.im), a.re} : CP{a.im, neg2(a.re)};
 }
 // multiply by e^{-+ i pi/4}
 template <bool INV>

@@ -434,6 +434,14 @@ k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float
   const int pair = blockIdx.x * CPB + c;
   const bool active = pair < npairs;
   CP* sh = reinterpret_cast<CP*>(smem_raw) + c * SH;
+  // the block's compliance rows, copied to shared memory while the forward FFT runs
+  float2* ksh = reinterpret_cast<float2*>(reinterpret_cast<CP*>(smem_raw) + CPB * SH);
+  {
+    const int pair0 = blockIdx.x * CPB;
+    const int nact = min(CPB, npairs - pair0);
+    const float2* src = tab2 + (size_t)pair0 * (N + 1);
+    for (int e = threadIdx.x; e < nact * (N + 1); e += CPB * TT) cp_async_elem(ksh + e, src + e);
+  }
   float4* col = spec4 + (size_t)pair * N;
   CP v[R];
 #pragma unroll
@@ -441,7 +449,9 @@ k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float
 #pragma unroll
   for (int q = R / 2; q < R; ++q) v[q] = pr::cp_zero();
   pr::pair_fft<LOGM, LOGR, false, true, CPB>(v, sh, twp, t, c);
-  const float2* kt = tab2 + (size_t)pair * (N + 1);
+  cp_async_wait_all();
+  __syncthreads();
+  const float2* kt = ksh + c * (N + 1);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int i = t + TT * q;
@@ -572,7 +582,7 @@ struct ColLaunch {
       constexpr int ppb = pairs_per_block<LOGN + 1, LOGR>();
       const int npairs = N / 2 + 1;
       const int grid = (npairs + ppb - 1) / ppb;
-      const size_t smem = (size_t)ppb * (PC::PADL + 8) * sizeof(pr::CP);
+      const size_t smem = (size_t)ppb * ((PC::PADL + 8) * sizeof(pr::CP) + (N + 1) * sizeof(float2));
       k_col_p<LOGN + 1, LOGR><<<grid, ppb * PC::T, smem, s>>>((float4*)k->ws.spec, (const float2*)k->ws.table,
                                                              (const float4*)k->ws.twpc, npairs, skip);
     } else {
