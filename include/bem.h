@@ -52,17 +52,30 @@ typedef enum {
 enum { BEM_FP64 = 0, BEM_FP32 = 1 };                   /* bem_kernel_desc.precision */
 enum { BEM_CTRL_DEPTH = 0, BEM_CTRL_FORCE = 1 };       /* bem_problem.control */
 enum { BEM_DC_FINITE_PART = 0, BEM_DC_ZERO = 1 };      /* bem_kernel_desc.dc_mode */
+enum { BEM_OP_PERIODIC = 0, BEM_OP_OPEN = 1 };        /* bem_kernel_desc.op_kind */
 
 /* Parameters of the discretised operator (Sec. 2): grid, cell size, layer and
  * substrate.  N is a power of two, 4 <= N <= 2048.  h may be INFINITY (homogeneous
- * E1, nu1), E2 may be INFINITY (rigid base; the paper's E2 = e^100).  0 <= nu < 0.5. */
+ * E1, nu1), E2 may be INFINITY (rigid base; the paper's E2 = e^100).  0 <= nu < 0.5.
+ *
+ * op_kind BEM_OP_PERIODIC (0): the paper's periodic product, Eq. (11), with the k = 0
+ * rule of dc_mode.  BEM_OP_OPEN (1): the non-periodic operator of a homogeneous
+ * half-space (h = INFINITY: E1, nu1; h = 0, or equal materials: E2, nu2): the
+ * surface displacement of a uniformly loaded square cell (the real-space form of
+ * Eq. 4 integrated over the cell, in closed form) convolved over the open plane, so
+ * that no periodic image and no k = 0 convention enter (dc_mode is ignored).  It is
+ * evaluated by the same FFT passes: the 2N-periodic wrap-around array of the cell
+ * coefficients (offsets up to N - 1, which is all a window of N cells uses) is
+ * transformed once, in double, into the compliance table.  A coating of a different
+ * material gives BEM_EUNSUPPORTED.  Building the table costs two double matrix
+ * products of order N + 1 (about 50 ms at N = 2048). */
 typedef struct {
   int32_t N;
   int32_t precision;    /* BEM_FP64: everything in double.  BEM_FP32: FFTs and vectors
                            in float; reductions, CG scalars and the detachment
                            test in double. */
   int32_t dc_mode;
-  int32_t reserved;
+  int32_t op_kind;      /* BEM_OP_PERIODIC or BEM_OP_OPEN (earlier versions: reserved, 0) */
   double delta, h, E1, nu1, E2, nu2;
 } bem_kernel_desc;
 

@@ -23,6 +23,7 @@ STATUS_NAMES = ["BEM_OK", "BEM_EINVAL", "BEM_ENOMEM", "BEM_ECUDA", "BEM_ENOCONV"
 BEM_FP64, BEM_FP32 = 0, 1
 BEM_CTRL_DEPTH, BEM_CTRL_FORCE = 0, 1
 BEM_DC_FINITE_PART, BEM_DC_ZERO = 0, 1
+BEM_OP_PERIODIC, BEM_OP_OPEN = 0, 1
 
 # entry points declared in include/bem.h
 EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
@@ -43,7 +44,7 @@ class BemError(RuntimeError):
 
 class KernelDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("precision", ctypes.c_int32), ("dc_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("delta", ctypes.c_double), ("h", ctypes.c_double),
+                ("op_kind", ctypes.c_int32), ("delta", ctypes.c_double), ("h", ctypes.c_double),
                 ("E1", ctypes.c_double), ("nu1", ctypes.c_double), ("E2", ctypes.c_double), ("nu2", ctypes.c_double)]
 
 
@@ -173,9 +174,10 @@ def _stream(stream):
 # ---------------------------------------------------------------------------
 # the C entry points, one to one
 
-def bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART, stream=None):
+def bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART, stream=None,
+                    op_kind=BEM_OP_PERIODIC):
     lib = load()
-    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, reserved=0, delta=delta, h=h, E1=E1, nu1=nu1,
+    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, op_kind=op_kind, delta=delta, h=h, E1=E1, nu1=nu1,
                    E2=E2, nu2=nu2)
     out = ctypes.c_void_p()
     _check(lib.bem_make_kernel(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
@@ -186,7 +188,7 @@ def bem_make_kernel_layers(N, delta, layers, E2, nu2, precision=BEM_FP64, dc_mod
     """Operator of a stack of bonded layers ``layers`` = [(h, E, nu), ...] from the
     surface down, on the substrate (E2, nu2)."""
     lib = load()
-    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, reserved=0, delta=delta, h=0.0, E1=1.0, nu1=0.0,
+    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, op_kind=0, delta=delta, h=0.0, E1=1.0, nu1=0.0,
                    E2=E2, nu2=nu2)
     n = len(layers)
     arr = (Layer * max(n, 1))(*[Layer(h=float(h), E=float(E), nu=float(nu)) for h, E, nu in layers])
@@ -259,7 +261,7 @@ def bem_matvec_static(N, delta, h, E1, nu1, E2, nu2, p, u, dc_mode=BEM_DC_FINITE
             if x.device.index != torch.cuda.current_device():
                 raise ValueError(f"bem_matvec_static: {name} is on {x.device}, the current device is "
                                  f"cuda:{torch.cuda.current_device()}")
-    d = KernelDesc(N=N, precision=BEM_FP32, dc_mode=dc_mode, reserved=0, delta=delta, h=h, E1=E1, nu1=nu1,
+    d = KernelDesc(N=N, precision=BEM_FP32, dc_mode=dc_mode, op_kind=0, delta=delta, h=h, E1=E1, nu1=nu1,
                    E2=E2, nu2=nu2)
     _check(load().bem_matvec_static(ctypes.byref(d), _ptr(p), _ptr(u), _stream(stream)))
     return u
@@ -298,9 +300,10 @@ class Kernel:
     """Owning wrapper of a bem_kernel handle (same parameters as bem_kernel_desc)."""
 
     def __init__(self, N, delta, h=None, E1=None, nu1=None, E2=1.0, nu2=0.3, precision="fp64",
-                 dc_mode=BEM_DC_FINITE_PART, stream=None, layers=None):
+                 dc_mode=BEM_DC_FINITE_PART, stream=None, layers=None, op_kind=BEM_OP_PERIODIC):
         """One coating (h, E1, nu1) on the substrate (E2, nu2), or, with ``layers`` =
-        [(h, E, nu), ...] from the surface down, a stack of coatings on it."""
+        [(h, E, nu), ...] from the surface down, a stack of coatings on it.  op_kind
+        BEM_OP_OPEN selects the non-periodic operator (homogeneous half-space only)."""
         self.N, self.delta = N, delta
         self.precision = precision
         prec = BEM_FP64 if precision == "fp64" else BEM_FP32
@@ -309,7 +312,7 @@ class Kernel:
             self.handle = bem_make_kernel_layers(N, delta, layers, E2, nu2, prec, dc_mode, stream)
         else:
             self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
-            self.handle = bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream)
+            self.handle = bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream, op_kind)
 
     @property
     def torch_dtype(self):

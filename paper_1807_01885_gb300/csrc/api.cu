@@ -52,6 +52,12 @@ bem_status check_desc(const bem_kernel_desc* d) {
     set_error("Poisson ratios must lie in [0, 0.5)");
     return BEM_EINVAL;
   }
+  if (d->op_kind != BEM_OP_PERIODIC && d->op_kind != BEM_OP_OPEN) { set_error("unknown op_kind"); return BEM_EINVAL; }
+  if (d->op_kind == BEM_OP_OPEN && !open_plane_homogeneous(*d)) {
+    set_error("the open-plane operator is built for a homogeneous half-space (h = INFINITY, h = 0 or equal "
+              "materials)");
+    return BEM_EUNSUPPORTED;
+  }
   return BEM_OK;
 }
 
@@ -393,6 +399,10 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
   }
   bem_status st = check_desc(desc);
   if (st != BEM_OK) return st;
+  if (n_layers > 0 && desc->op_kind == BEM_OP_OPEN) {
+    set_error("the open-plane operator is built for a homogeneous half-space, not a coating stack");
+    return BEM_EUNSUPPORTED;
+  }
   bem_kernel_s* k = new bem_kernel_s();
   k->desc = *desc;
   k->n_layers = n_layers;

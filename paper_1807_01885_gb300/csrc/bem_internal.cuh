@@ -180,6 +180,19 @@ cudaStream_t capture_stream();
 uint64_t next_serial();
 // api.cu: BEM_OK when the description is valid, else BEM_EINVAL with a message
 bem_status check_desc(const bem_kernel_desc* d);
+// the open-plane operator's body is homogeneous: h = INFINITY (E1, nu1), h = 0 (E2,
+// nu2) or both materials equal; *E, *nu receive its modulus and Poisson ratio
+inline bool open_plane_homogeneous(const bem_kernel_desc& d, double* E = nullptr, double* nu = nullptr) {
+  double e = 0.0, n = 0.0;
+  bool ok = true;
+  if (d.h == INFINITY) { e = d.E1; n = d.nu1; }
+  else if (d.h == 0.0 || (d.E1 == d.E2 && d.nu1 == d.nu2)) { e = d.E2; n = d.nu2; }
+  else ok = false;
+  if (ok && !(e > 0.0 && e < INFINITY)) ok = false;
+  if (E != nullptr) *E = e;
+  if (nu != nullptr) *nu = n;
+  return ok;
+}
 
 // matvec.cu
 bem_status build_table(bem_kernel_s* k, cudaStream_t s);

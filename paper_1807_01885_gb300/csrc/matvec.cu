@@ -73,6 +73,109 @@ __global__ void k_table64_stack(double* __restrict__ t64, Stack st, double kstep
   t64[(size_t)i * (N + 1) + j] = val;
 }
 
+// ---------------------------------------------------------------------------
+// Open-plane operator of a homogeneous half-space.  The displacement at (x, y) of a
+// uniform unit pressure on the square cell |xi|, |eta| <= delta/2 is Boussinesq's
+// point-load solution 1/(pi E* r) (Eq. 4 in real space) integrated over the cell; the
+// double integral of 1/r has the closed form (Love)
+//   I(x, y) = F(x+h, y+h) - F(x+h, y-h) - F(x-h, y+h) + F(x-h, y-h),  h = delta/2,
+//   F(s, t) = s asinh(t/|s|) + t asinh(s/|t|)   (a term is 0 where its s or t is 0).
+// The window products only use offsets |dx|, |dy| <= N - 1, so the 2N-periodic
+// wrap-around array W of the coefficients (zero at offset N) gives the open-plane
+// convolution exactly; its 2-D DFT is real and even, K(i, j) = sum_{x, y} w_x w_y
+// G(x, y) cos(pi i x / N) cos(pi j y / N) over x, y in [0, N] (w_0 = 1, w = 2
+// inside, w_N = 0), i.e. K = C Gw C^T with C[i][x] = cos(pi i x / N): two double
+// matrix products of order N + 1.
+__device__ double love_f(double s, double t) {
+  const double a = (s != 0.0) ? s * asinh(t / fabs(s)) : 0.0;
+  const double b = (t != 0.0) ? t * asinh(s / fabs(t)) : 0.0;
+  return a + b;
+}
+
+__global__ void k_open_coef(double* __restrict__ gw, int N, double delta, double inv_pi_es) {
+  const size_t n1 = (size_t)N + 1, total = n1 * n1;
+  const double h = 0.5 * delta;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n1), j = (int)(idx % n1);
+    double v = 0.0;
+    if (i < N && j < N) {
+      const double x = i * delta, y = j * delta;
+      const double I = love_f(x + h, y + h) - love_f(x + h, y - h) - love_f(x - h, y + h) + love_f(x - h, y - h);
+      v = (i == 0 ? 1.0 : 2.0) * (j == 0 ? 1.0 : 2.0) * I * inv_pi_es;
+    }
+    gw[idx] = v;
+  }
+}
+
+__global__ void k_cos_mat(double* __restrict__ cm, int N) {
+  const size_t n1 = (size_t)N + 1, total = n1 * n1;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const long long i = (long long)(idx / n1), x = (long long)(idx % n1);
+    cm[idx] = cospi((double)((i * x) % (2 * N)) / (double)N);
+  }
+}
+
+// Cout[m][n] = sum_k A[m][k] B[n][k] for n x n row-major matrices (double; 64 x 64
+// output tiles, 4 x 4 per thread, k in steps of 16 through shared memory)
+__global__ void __launch_bounds__(256) k_dgemm_nt(const double* __restrict__ A, const double* __restrict__ B,
+                                                  double* __restrict__ Cout, int n) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      const int r = e / 16, kk = e % 16;
+      const int m = m0 + r, nn = n0 + r, k = k0 + kk;
+      As[kk][r] = (m < n && k < n) ? A[(size_t)m * n + k] : 0.0;
+      Bs[kk][r] = (nn < n && k < n) ? B[(size_t)nn * n + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty + 16 * q];
+        b[q] = Bs[kk][tx + 16 * q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[q][r] = fma(a[q], b[r], acc[q][r]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int m = m0 + ty + 16 * q, nn = n0 + tx + 16 * r;
+      if (m < n && nn < n) Cout[(size_t)m * n + nn] = acc[q][r];
+    }
+}
+
+// The open-plane table into k->ws.table64; the handle's spectrum and solver vectors
+// (unused until the first product) hold the intermediate matrices.
+static bem_status build_open_table(bem_kernel_s* k, cudaStream_t s) {
+  double E = 0.0, nu = 0.0;
+  open_plane_homogeneous(k->desc, &E, &nu);
+  const double es = E / (1.0 - nu * nu);
+  const int n = k->N + 1;
+  double* cm = (double*)k->ws.spec;
+  double* gw = (double*)k->ws.vec;
+  double* u = gw + (size_t)n * n;
+  k_open_coef<<<256, 256, 0, s>>>(gw, k->N, k->desc.delta, 1.0 / (M_PI * es));
+  k_cos_mat<<<256, 256, 0, s>>>(cm, k->N);
+  const dim3 grid((n + 63) / 64, (n + 63) / 64);
+  k_dgemm_nt<<<grid, 256, 0, s>>>(cm, gw, u, n);              // U = C Gw (Gw is symmetric)
+  k_dgemm_nt<<<grid, 256, 0, s>>>(u, cm, k->ws.table64, n);   // K = U C^T
+  note_launches(4);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
 // The stack of a handle in the scaled form of stack.cuh.
 static Stack stack_of(const bem_kernel_s* k) {
   Stack st{};
@@ -200,7 +303,10 @@ bem_status build_table(bem_kernel_s* k, cudaStream_t s) {
     P.dc = P.c_pref * d.h * (dn * d0 - n0 * dd) / (d0 * d0);
   }
   dim3 grid((k->N + 1 + 127) / 128, k->N + 1);
-  if (k->n_layers > 0) {
+  if (d.op_kind == BEM_OP_OPEN) {
+    bem_status st = build_open_table(k, s);
+    if (st != BEM_OK) return st;
+  } else if (k->n_layers > 0) {
     // stack: the long-wave expansion phi(eps) = phi(0) + phi'(0) eps by dual numbers
     const Stack st = stack_of(k);
     const double dc = (d.dc_mode == BEM_DC_ZERO) ? 0.0 : stack_phi<Dual>(st, Dual{0.0, 1.0}).d;

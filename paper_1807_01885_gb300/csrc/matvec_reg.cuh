@@ -266,11 +266,13 @@ __host__ __device__ constexpr int row_pairs_per_block() {
   constexpr int c = RowPairCfg<LOGR>::MAXT / Plan<LOGN, LOGR>::T;
   return c < 1 ? 1 : (c > (1 << (LOGN - 1)) ? (1 << (LOGN - 1)) : c);
 }
-// CP slots of one pair's shared buffer: the padded exchange buffer plus 8; it also
-// holds the pair's two rows of (N/2 + 1) spectrum records in the inverse pass
+// CP slots of one pair's shared buffer: the padded exchange buffer plus 9; it also
+// holds the pair's two rows of (N/2 + 1) spectrum records in the inverse pass.  The
+// odd count puts the buffers of neighbouring pairs in different 16-byte bank groups
+// (the forward pass's recombination reads the same index from two buffers at once).
 template <int LOGN, int LOGR>
 __host__ __device__ constexpr int row_pair_sh() {
-  return Plan<LOGN, LOGR>::PADL + 8;
+  return Plan<LOGN, LOGR>::PADL + 9;
 }
 
 template <int LOGN, int LOGR>
@@ -365,23 +367,42 @@ k_row_inv_p(const float4* __restrict__ spec4, float* __restrict__ u, const float
   }
   cp_async_wait_all();
   __syncthreads();
-  // Zi[j] = (Y[j] + Y*[N-j]) + i e^{+i pi j/N} (Y[j] - Y*[N-j]) for both rows
-  const float* ba = reinterpret_cast<const float*>(sh);
-  const float* bb = ba + 4 * NP;
+  // Zi[j] = (Y[j] + Y*[N-j]) + i e^{+i pi j/N} (Y[j] - Y*[N-j]) for both rows.
+  // Thread t forms the frequency pairs jp = t + TT q (q < R/2), j = 2 jp and 2 jp + 1,
+  // from the records jp of both rows and their mirrors: N - 2 jp lies in record
+  // N/2 - jp (first of its two frequencies), N - 2 jp - 1 in record N/2 - jp - 1
+  // (second).  The values then go through the buffer to the FFT's input layout.
+  const float4* ra = reinterpret_cast<const float4*>(sh);
+  const float4* rbk = ra + NP;
   CP v[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int j = t + TT * q, jr = N - j;
-    const int ia = 4 * (j >> 1) + (j & 1), ir = 4 * (jr >> 1) + (jr & 1);
-    const CP y1 = CP{pr::pk2(ba[ia], bb[ia]), pr::pk2(ba[ia + 2], bb[ia + 2])};
-    const CP y2 = CP{pr::pk2(ba[ir], bb[ir]), pr::pk2(ba[ir + 2], bb[ir + 2])};   // conjugated below
-    // e = y1 + conj y2, d = y1 - conj y2; o = i conj(w) d with w = e^{-i pi j/N}
+  auto recomb = [&](CP y1, CP y2, int j) -> CP {
+    // e = y1 + conj y2, d = y1 - conj y2; Zi = e + i conj(w) d with w = e^{-i pi j/N}
     const CP ev = CP{pr::add2(y1.re, y2.re), pr::sub2(y1.im, y2.im)};
     const CP d = CP{pr::sub2(y1.re, y2.re), pr::add2(y1.im, y2.im)};
     const CP dw = pr::twmul<true>(d, pr::tw_load(rb4 + j));
-    v[q] = CP{pr::sub2(ev.re, dw.im), pr::add2(ev.im, dw.re)};
+    return CP{pr::sub2(ev.re, dw.im), pr::add2(ev.im, dw.re)};
+  };
+#pragma unroll
+  for (int q = 0; q < R / 2; ++q) {
+    const int jp = t + TT * q;
+    const float4 a = ra[jp], b = rbk[jp];
+    const float4 am = ra[N / 2 - jp], bm = rbk[N / 2 - jp];
+    const float4 an = ra[N / 2 - jp - 1], bn = rbk[N / 2 - jp - 1];
+    v[2 * q] = recomb(CP{pr::pk2(a.x, b.x), pr::pk2(a.z, b.z)}, CP{pr::pk2(am.x, bm.x), pr::pk2(am.z, bm.z)}, 2 * jp);
+    v[2 * q + 1] = recomb(CP{pr::pk2(a.y, b.y), pr::pk2(a.w, b.w)}, CP{pr::pk2(an.y, bn.y), pr::pk2(an.w, bn.w)},
+                          2 * jp + 1);
   }
-  __syncthreads();
+  GroupSync<TT, PPB>::sync(pl);   // every record of the pair read
+#pragma unroll
+  for (int q = 0; q < R / 2; ++q) {
+    const int jp = t + TT * q;
+    sh[padi<LOGR>(2 * jp)] = v[2 * q];
+    sh[padi<LOGR>(2 * jp + 1)] = v[2 * q + 1];
+  }
+  GroupSync<TT, PPB>::sync(pl);
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = sh[padi<LOGR>(t + TT * q)];
+  GroupSync<TT, PPB>::sync(pl);   // read before the FFT's first exchange overwrites
   pr::pair_fft<LOGN, LOGR, true, false, PPB>(v, sh, twpr, t, pl);
   // z[m] = u[2m] + i u[2m+1] of each row, first N/2 values
   float2* ua = reinterpret_cast<float2*>(u + (size_t)(r0 + 2 * pl) * N);

@@ -113,6 +113,10 @@ extern "C" bem_status bem_matvec_static(const bem_kernel_desc* desc, const float
     set_error("bem_matvec_static: only precision BEM_FP32 is available");
     return BEM_EINVAL;
   }
+  if (desc->op_kind != BEM_OP_PERIODIC) {
+    set_error("bem_matvec_static: only the periodic operator (op_kind BEM_OP_PERIODIC) is available");
+    return BEM_EINVAL;
+  }
   if (((uintptr_t)p & 15) != 0 || ((uintptr_t)u & 15) != 0) {
     set_error("bem_matvec_static: p and u must be 16-byte aligned");
     return BEM_EINVAL;

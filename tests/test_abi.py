@@ -122,7 +122,7 @@ def test_argument_errors_before_any_device_call(bemlib):
     u = np.zeros_like(p)
 
     def static(N, p_, u_, nu1=0.3, E1=1.0, precision=bem.BEM_FP32):
-        d = bem.KernelDesc(N=N, precision=precision, dc_mode=0, reserved=0, delta=0.1, h=1.0, E1=E1, nu1=nu1,
+        d = bem.KernelDesc(N=N, precision=precision, dc_mode=0, op_kind=0, delta=0.1, h=1.0, E1=E1, nu1=nu1,
                            E2=1.0, nu2=0.3)
         st = bemlib.bem_matvec_static(ctypes.byref(d), bem._ptr(p_), bem._ptr(u_), None)
         return st, bemlib.bem_last_error().decode()
