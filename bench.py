@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batch workload (0: skip)")
-    ap.add_argument("--warmstart", type=int, default=512,
+    ap.add_argument("--warmstart-steps", type=int, default=2000, help="training steps of the learned warm start")
+    ap.add_argument("--warmstart-test", type=int, default=16, help="held-out N=2048 instances of the warm start")
+    ap.add_argument("--warmstart", type=int, default=20000,
                     help="training solutions for the learned warm start (0: skip)")
     ap.add_argument("--adhesive", type=int, default=1,
                     help="run the adhesive ramp workload (N=512, 200 steps, FP32; 0: skip)")
@@ -431,10 +433,13 @@ WS_TRAIN_SEED0 = 30000000
 WS_TEST_SEED0 = 40000000
 
 
-def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
-    """Learned warm start: the network is trained here on n_train solver solutions at
-    N = 256 (rough-surface workload), then seeds FP32 solves at N = 2048 of n_test
-    held-out instances; cold and seeded solves to 1e-8 are timed on one stream."""
+def warm_start_bench(torch, dev, bem, n_train, steps, n_test, batch=16):
+    """Learned warm start (the learned-warm-start workload): the network (4 layers,
+    width 32, 16 modes) is trained here on n_train solver solutions at N = 256 of the
+    rough-surface workload (seeds 30000000 + i), then seeds FP32 force-controlled solves
+    to 1e-8 of n_test held-out N = 2048 instances (seeds 40000000 + i).  Timed on one
+    stream: cold and seeded solves one after another and batched, the network's
+    inference separately; and the same at the training resolution (32 instances)."""
     from paper_1807_01885_gb300 import warmstart
     net = bem.Fno(width=32, modes=16, layers=4, hidden=64)
     rng = np.random.default_rng(7)
@@ -446,40 +451,81 @@ def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
                            rng.standard_normal(64) / 8.0, np.zeros(1)]).astype(np.float32)
     assert init.size == cnt
     net.set_params(torch.tensor(init, device=dev))
-    insts = warmstart.default_instances(n_train, 256, WS_TRAIN_SEED0)
+    Nt = 256
     t0 = time.perf_counter()
-    xs, qs = [], []
-    for c in range(0, n_train, 128):
-        x, q, _ = warmstart.make_dataset(net, insts[c:c + 128], dev)
-        xs.append(x)
-        qs.append(q)
-    x, q = torch.cat(xs), torch.cat(qs)
+    insts = warmstart.default_instances(n_train, Nt, WS_TRAIN_SEED0)
+    t_gen = time.perf_counter() - t0
+    # training set: solver solutions of every instance, a pool of handles rebuilt in place
+    t0 = time.perf_counter()
+    chunk = 256
+    pool = [bem.Kernel(Nt, 1.0 / Nt, 0.1, 1.0, 0.3, 1.0, 0.3, precision="fp32") for _ in range(min(chunk, n_train))]
+    x = torch.empty((n_train, 7, Nt, Nt), dtype=torch.float32, device=dev)
+    q = torch.empty((n_train, Nt, Nt), dtype=torch.float32, device=dev)
+    iters_train = []
+    for c in range(0, n_train, chunk):
+        xc, qc, res = warmstart.make_dataset(net, insts[c:c + chunk], dev, kernels=pool)
+        x[c:c + xc.shape[0]].copy_(xc)
+        q[c:c + qc.shape[0]].copy_(qc)
+        iters_train += [r["iters"] for r in res]
+        del xc, qc
+    for k in pool:
+        k.close()
+    torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    losses = warmstart.train(net, x, q, steps=steps, batch=8, lr=2e-3, lr_final=1e-4)
+    losses = warmstart.train(net, x, q, steps=steps, batch=batch, lr=2e-3, lr_final=1e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    del x, q, xs, qs
+    del x, q
+    torch.cuda.empty_cache()
     test = warmstart.default_instances(n_test, N_GRID, WS_TEST_SEED0)
     heights, params, pbar = warmstart.instance_tensors(test, dev)
     s = torch.cuda.Stream(device=dev)
+    ks = [bem.Kernel(i["N"], i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"], precision="fp32")
+          for i in test]
+    outs = torch.empty_like(heights)
+
+    def one_by_one(p_init=None):
+        rs = []
+        for kk, i, b in zip(ks, test, range(len(test))):
+            rs.append(kk.solve(heights[b], "force", i["force"], tol=TOL, p_init=None if p_init is None else p_init[b],
+                               p_out=outs[b], stream=s)[1])
+        s.synchronize()
+        return rs
+
+    def batched(p_init=None):
+        probs = [bem.make_problem(heights[b], bem.BEM_CTRL_FORCE, test[b]["force"], tol=TOL, max_iter=5000,
+                                  p_init=None if p_init is None else p_init[b]) for b in range(len(test))]
+        _, rs = bem.bem_solve_batch([kk.handle for kk in ks], probs, [outs[b] for b in range(len(test))], stream=s)
+        s.synchronize()
+        return rs
+
     with torch.cuda.stream(s):
-        warmstart.solve_all(test, heights, stream=s)                     # graph capture, warm caches
-        s.synchronize()
+        one_by_one()                                                     # graph capture, warm caches
+        batched()
+        p_w = warmstart.predict(net, heights, params, pbar)
+        one_by_one(p_w)
+        batched(p_w)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, r_cold = warmstart.solve_all(test, heights, stream=s)
-        s.synchronize()
+        r_cold = one_by_one()
         t_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rb_cold = batched()
+        t_cold_b = time.perf_counter() - t0
         t0 = time.perf_counter()
         p_init = warmstart.predict(net, heights, params, pbar)
         torch.cuda.synchronize()
         t_pred = time.perf_counter() - t0
         t0 = time.perf_counter()
-        _, r_warm = warmstart.solve_all(test, heights, p_init=p_init, stream=s)
-        s.synchronize()
+        r_warm = one_by_one(p_init)
         t_warm = time.perf_counter() - t0
-        # the same at the training resolution: 32 held-out N = 256 instances, batched
-        small = warmstart.default_instances(32, 256, WS_TEST_SEED0)
+        t0 = time.perf_counter()
+        p_init = warmstart.predict(net, heights, params, pbar)
+        rb_warm = batched(p_init)
+        t_warm_b = time.perf_counter() - t0
+        # the same at the training resolution: 32 held-out N = 256 instances
+        small = warmstart.default_instances(32, Nt, WS_TEST_SEED0)
         hs, ps, pbs = warmstart.instance_tensors(small, dev)
         warmstart.solve_all(small, hs, stream=s)
         s.synchronize()
@@ -489,52 +535,33 @@ def warm_start_bench(torch, dev, bem, n_train, steps, n_test):
         ts_cold = time.perf_counter() - t0
         t0 = time.perf_counter()
         ps_init = warmstart.predict(net, hs, ps, pbs)
-        torch.cuda.synchronize()
-        ts_pred = time.perf_counter() - t0
-        t0 = time.perf_counter()
         _, rs_warm = warmstart.solve_all(small, hs, p_init=ps_init, stream=s)
         s.synchronize()
         ts_warm = time.perf_counter() - t0
-        # the same instances solved one after another (latency, not throughput):
-        # cold, then prediction for all of them plus seeded solves
-        ks = [bem.Kernel(i["N"], i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"], precision="fp32")
-              for i in small]
-        outs = torch.empty_like(hs)
-        for kk, i, b in zip(ks, small, range(len(small))):       # graph capture
-            kk.solve(hs[b], "force", i["force"], tol=TOL, p_out=outs[b], stream=s)
-        s.synchronize()
-        t0 = time.perf_counter()
-        for kk, i, b in zip(ks, small, range(len(small))):
-            kk.solve(hs[b], "force", i["force"], tol=TOL, p_out=outs[b], stream=s)
-        s.synchronize()
-        tq_cold = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        pq = warmstart.predict(net, hs, ps, pbs)
-        for kk, i, b in zip(ks, small, range(len(small))):
-            kk.solve(hs[b], "force", i["force"], tol=TOL, p_init=pq[b], p_out=outs[b], stream=s)
-        s.synchronize()
-        tq_warm = time.perf_counter() - t0
-        for kk in ks:
-            kk.close()
+    for kk in ks:
+        kk.close()
     net.close()
-    at_train_res = {"N": 256, "instances": len(small), "seeds": f"{WS_TEST_SEED0}..{WS_TEST_SEED0 + len(small) - 1}",
-                    "cold_iters_mean": float(np.mean([r["iters"] for r in rs_cold])),
-                    "warm_iters_mean": float(np.mean([r["iters"] for r in rs_warm])),
-                    "cold_batch_ms": 1000 * ts_cold, "warm_batch_ms": 1000 * ts_warm,
-                    "inference_ms": 1000 * ts_pred,
-                    "sequential_cold_ms": 1000 * tq_cold,
-                    "sequential_inference_plus_warm_ms": 1000 * tq_warm,
-                    "all_converged": all(r["status"] == 0 for r in rs_cold + rs_warm)}
-    return {"train_samples": n_train, "train_N": 256, "train_steps": steps, "batch": 8,
-            "q_min": 1.0, "at_training_resolution": at_train_res,
-            "data_s": t_data, "train_s": t_train,
+    it = lambda rs: [r["iters"] for r in rs]
+    return {"train_samples": n_train, "train_N": Nt, "train_steps": steps, "batch": batch,
+            "train_seeds": f"{WS_TRAIN_SEED0}..{WS_TRAIN_SEED0 + n_train - 1}", "q_min": 1.0,
+            "generate_s": t_gen, "data_s": t_data, "train_s": t_train,
+            "train_solve_iters_mean": float(np.mean(iters_train)),
             "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
             "test_N": N_GRID, "test_instances": n_test, "test_seeds": f"{WS_TEST_SEED0}..{WS_TEST_SEED0 + n_test - 1}",
-            "cold_ms_per_solve": 1000 * t_cold / n_test, "inference_ms_per_solve": 1000 * t_pred / n_test,
-            "warm_ms_per_solve": 1000 * t_warm / n_test,
-            "warm_plus_inference_ms_per_solve": 1000 * (t_warm + t_pred) / n_test,
-            "cold_iters": [r["iters"] for r in r_cold], "warm_iters": [r["iters"] for r in r_warm],
-            "all_converged": all(r["status"] == 0 for r in r_cold + r_warm)}
+            "inference_ms_per_instance": 1000 * t_pred / n_test,
+            "one_after_another": {"cold_ms_per_solve": 1000 * t_cold / n_test,
+                                  "warm_plus_inference_ms_per_solve": 1000 * (t_warm + t_pred) / n_test,
+                                  "cold_iters_mean": float(np.mean(it(r_cold))),
+                                  "warm_iters_mean": float(np.mean(it(r_warm)))},
+            "batched": {"cold_ms_per_solve": 1000 * t_cold_b / n_test,
+                        "warm_plus_inference_ms_per_solve": 1000 * t_warm_b / n_test,
+                        "cold_iters_mean": float(np.mean(it(rb_cold))),
+                        "warm_iters_mean": float(np.mean(it(rb_warm)))},
+            "at_training_resolution": {"N": Nt, "instances": len(small),
+                                       "cold_batch_ms": 1000 * ts_cold, "warm_plus_inference_batch_ms": 1000 * ts_warm,
+                                       "cold_iters_mean": float(np.mean(it(rs_cold))),
+                                       "warm_iters_mean": float(np.mean(it(rs_warm)))},
+            "all_converged": all(r["status"] == 0 for r in r_cold + r_warm + rb_cold + rb_warm + rs_cold + rs_warm)}
 
 
 _ORACLE_CASE = {}
@@ -776,7 +803,7 @@ def run_ours(args):
     if args.punch > 0:
         line["punch_sweep"] = punch_sweep_bench(torch, dev, bem, inputs)
     if args.warmstart > 0:
-        line["warm_start"] = warm_start_bench(torch, dev, bem, args.warmstart, 1500, 2)
+        line["warm_start"] = warm_start_bench(torch, dev, bem, args.warmstart, args.warmstart_steps, args.warmstart_test)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt = cpu_oracle_matvecs()
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -149,6 +149,15 @@ typedef struct {
 bem_status bem_make_kernel_layers(const bem_kernel_desc* desc, int32_t n_layers, const bem_layer* layers,
                                   void* cuda_stream, bem_kernel* out);
 
+/* Rebuilds an existing handle's operator for new parameters in place: desc->N and
+ * desc->precision must equal the handle's (BEM_EINVAL otherwise); delta, h, E1, nu1,
+ * E2, nu2, dc_mode and op_kind may change (a coating stack made by
+ * bem_make_kernel_layers becomes the single coating of desc).  Allocates nothing and
+ * keeps the handle's captured iteration graphs valid (they read the table in place),
+ * so a pool of handles can serve a stream of instances of one grid size, as the
+ * learned warm start's training-set generation does.  Synchronises the stream. */
+bem_status bem_rebuild_kernel(bem_kernel k, const bem_kernel_desc* desc, void* cuda_stream);
+
 /* Copies the double-precision compliance table K^(k_ij), i, j in [0, N], row-major
  * (N+1)*(N+1) doubles, in m/Pa-consistent units (no FFT normalisation), to out
  * (host or device).  Entry (0,0) is the DC value chosen by dc_mode. */

@@ -31,7 +31,7 @@ EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_mat
            "bem_launch_count", "bem_last_error", "bem_version", "bem_fno_create", "bem_fno_destroy",
            "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features", "bem_fno_forward",
            "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure", "bem_set_radix",
-           "bem_autotune", "bem_make_kernel_layers")
+           "bem_autotune", "bem_make_kernel_layers", "bem_rebuild_kernel")
 BEM_MAX_LAYERS = 8
 BEM_STATIC_MAX_N = 256
 
@@ -91,6 +91,8 @@ def load(path=None):
     lib.bem_make_kernel_layers.argtypes = [ctypes.POINTER(KernelDesc), i32, ctypes.POINTER(Layer), vp,
                                            ctypes.POINTER(vp)]
     lib.bem_make_kernel_layers.restype = i32
+    lib.bem_rebuild_kernel.argtypes = [vp, ctypes.POINTER(KernelDesc), vp]
+    lib.bem_rebuild_kernel.restype = i32
     lib.bem_destroy_kernel.argtypes = [vp]
     lib.bem_kernel_table.argtypes = [vp, vp, vp]
     lib.bem_matvec.argtypes = [vp, vp, vp, vp]
@@ -184,17 +186,25 @@ def bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, precision=BEM_FP64, dc_mode=B
     return out.value
 
 
-def bem_make_kernel_layers(N, delta, layers, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART, stream=None):
+def bem_make_kernel_layers(N, delta, layers, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART, stream=None,
+                           op_kind=BEM_OP_PERIODIC):
     """Operator of a stack of bonded layers ``layers`` = [(h, E, nu), ...] from the
     surface down, on the substrate (E2, nu2)."""
     lib = load()
-    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, op_kind=0, delta=delta, h=0.0, E1=1.0, nu1=0.0,
+    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, op_kind=op_kind, delta=delta, h=0.0, E1=1.0, nu1=0.0,
                    E2=E2, nu2=nu2)
     n = len(layers)
     arr = (Layer * max(n, 1))(*[Layer(h=float(h), E=float(E), nu=float(nu)) for h, E, nu in layers])
     out = ctypes.c_void_p()
     _check(lib.bem_make_kernel_layers(ctypes.byref(d), n, arr, _stream(stream), ctypes.byref(out)))
     return out.value
+
+
+def bem_rebuild_kernel(k, N, delta, h, E1, nu1, E2, nu2, precision=BEM_FP64, dc_mode=BEM_DC_FINITE_PART,
+                       stream=None, op_kind=BEM_OP_PERIODIC):
+    d = KernelDesc(N=N, precision=precision, dc_mode=dc_mode, op_kind=op_kind, delta=delta, h=h, E1=E1, nu1=nu1,
+                   E2=E2, nu2=nu2)
+    _check(load().bem_rebuild_kernel(k, ctypes.byref(d), _stream(stream)))
 
 
 def bem_destroy_kernel(k):
@@ -309,7 +319,7 @@ class Kernel:
         prec = BEM_FP64 if precision == "fp64" else BEM_FP32
         if layers is not None:
             self.params = dict(layers=[tuple(x) for x in layers], E2=E2, nu2=nu2)
-            self.handle = bem_make_kernel_layers(N, delta, layers, E2, nu2, prec, dc_mode, stream)
+            self.handle = bem_make_kernel_layers(N, delta, layers, E2, nu2, prec, dc_mode, stream, op_kind)
         else:
             self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
             self.handle = bem_make_kernel(N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream, op_kind)
@@ -343,6 +353,14 @@ class Kernel:
         prob = make_problem(height, ctrl, target, dgamma, tol, max_iter, p_init, contact_mask)
         res = bem_solve_contact(self.handle, prob, p_out, stream)
         return p_out, res
+
+    def rebuild(self, delta, h, E1, nu1, E2, nu2, dc_mode=BEM_DC_FINITE_PART, stream=None,
+                op_kind=BEM_OP_PERIODIC):
+        """New operator parameters on the same grid size and precision, in place."""
+        prec = BEM_FP64 if self.precision == "fp64" else BEM_FP32
+        bem_rebuild_kernel(self.handle, self.N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream, op_kind)
+        self.delta = delta
+        self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
 
     def set_radix(self, rows, cols, stream=None):
         """log2 of the FFT radix of the row and column passes (3 or 4; 3 only in fp64)."""

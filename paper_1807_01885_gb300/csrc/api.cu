@@ -485,6 +485,24 @@ bem_status bem_make_kernel_layers(const bem_kernel_desc* desc, int32_t n_layers,
   return make_kernel(desc, n_layers, layers, cuda_stream, out);
 }
 
+bem_status bem_rebuild_kernel(bem_kernel k, const bem_kernel_desc* desc, void* cuda_stream) {
+  if (k == nullptr) { set_error("NULL kernel"); return BEM_EINVAL; }
+  bem_status st = check_desc(desc);
+  if (st != BEM_OK) return st;
+  if (desc->N != k->N || desc->precision != k->prec) {
+    set_error("bem_rebuild_kernel: N and precision must equal the handle's");
+    return BEM_EINVAL;
+  }
+  DeviceGuard g(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  k->desc = *desc;
+  k->n_layers = 0;
+  st = build_table(k, s);
+  if (st != BEM_OK) return st;
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
 bem_status bem_destroy_kernel(bem_kernel k) {
   if (k == nullptr) return BEM_OK;
   DeviceGuard g(k->dev);

@@ -83,3 +83,50 @@ def batch_instance(seed, sizes=(128, 256, 512, 1024)):
     pbar = 0.025 * 0.1 * es
     force = pbar * (N * delta) ** 2
     return dict(N=N, delta=delta, h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2, height=f, force=force)
+
+
+def _heights_chunk(args):
+    """Worker of ``batch_heights``: instances [i0, i1) at grid size N; the height maps
+    go into the named shared-memory array, the scalars come back."""
+    from multiprocessing import shared_memory
+    name, count, N, seed0, i0, i1 = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        out = np.ndarray((count, N, N), dtype=np.float32, buffer=shm.buf)
+        scalars = []
+        for i in range(i0, i1):
+            inst = batch_instance(seed0 + i, sizes=(N,))
+            out[i] = inst.pop("height")
+            scalars.append(inst)
+        del out
+        return scalars
+    finally:
+        shm.close()
+
+
+def batch_heights(count, N, seed0, workers=None, timeout=900.0):
+    """``count`` instances of the batch workload at grid size N (seeds seed0 + i), the
+    same draws as ``batch_instance``, made on the host cores in parallel: returns
+    (heights float32 [count, N, N], per-instance scalar dicts).  Workers start with
+    'spawn' (the caller may hold a CUDA context) and write into shared memory; a
+    failed pool or one slower than ``timeout`` seconds raises."""
+    import concurrent.futures as cf
+    import multiprocessing
+    import os
+    from multiprocessing import shared_memory
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    if workers == 1 or count * N * N < (1 << 21):
+        insts = [batch_instance(seed0 + i, sizes=(N,)) for i in range(count)]
+        return np.stack([i.pop("height") for i in insts]).astype(np.float32), insts
+    shm = shared_memory.SharedMemory(create=True, size=count * N * N * 4)
+    try:
+        bounds = np.linspace(0, count, 4 * workers + 1).astype(int)
+        jobs = [(shm.name, count, N, seed0, int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        with cf.ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            futs = [ex.submit(_heights_chunk, j) for j in jobs]
+            parts = [f.result(timeout=timeout) for f in futs]
+        heights = np.ndarray((count, N, N), dtype=np.float32, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    return heights, [inst for part in parts for inst in part]

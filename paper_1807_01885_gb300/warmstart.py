@@ -28,25 +28,35 @@ def instance_tensors(insts, device):
     return heights, params, pbar
 
 
-def solve_all(insts, heights, p_init=None, tol=1e-8, max_iter=5000, stream=None):
+def solve_all(insts, heights, p_init=None, tol=1e-8, max_iter=5000, stream=None, kernels=None):
     """Solves every instance (force control, float) with one batched call; returns
-    (pressures [B, N, N], results)."""
-    ks = [bem.Kernel(i["N"], i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"], precision="fp32")
-          for i in insts]
+    (pressures [B, N, N], results).  ``kernels``: reusable float handles of the grid
+    size (rebuilt in place for each instance); by default one handle per instance."""
+    own = kernels is None
+    if own:
+        ks = [bem.Kernel(i["N"], i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"], precision="fp32")
+              for i in insts]
+    else:
+        ks = kernels[:len(insts)]
+        for k, i in zip(ks, insts):
+            k.rebuild(i["delta"], i["h"], i["E1"], i["nu1"], i["E2"], i["nu2"])
     outs = torch.empty_like(heights)
     probs = [bem.make_problem(heights[b], bem.BEM_CTRL_FORCE, insts[b]["force"], tol=tol, max_iter=max_iter,
                               p_init=None if p_init is None else p_init[b]) for b in range(len(insts))]
     st, res = bem.bem_solve_batch([k.handle for k in ks], probs, [outs[b] for b in range(len(insts))],
                                   stream=stream)
-    for k in ks:
-        k.close()
+    if own:
+        for k in ks:
+            k.close()
     return outs, res
 
 
-def make_dataset(fno, insts, device, tol=1e-8):
-    """Features x [B, 7, N, N] and targets q [B, N, N] from solver solutions."""
+def make_dataset(fno, insts, device, tol=1e-8, kernels=None):
+    """Features x [B, 7, N, N] and targets q [B, N, N] from solver solutions; ``kernels``
+    (optional, at least B handles of the grid size) are rebuilt in place instead of
+    creating one handle per instance."""
     heights, params, pbar = instance_tensors(insts, device)
-    p, res = solve_all(insts, heights, tol=tol)
+    p, res = solve_all(insts, heights, tol=tol, kernels=kernels)
     B, N = heights.shape[0], heights.shape[-1]
     x = torch.empty((B, 7, N, N), dtype=torch.float32, device=device)
     fno.features(B, N, heights, params, x)
@@ -97,6 +107,9 @@ def predict(fno, heights, params, pbar, q_min=1.0):
     return p
 
 
-def default_instances(count, N, seed0):
-    """Rough-surface batch-workload instances at one grid size."""
-    return [inputs.batch_instance(seed0 + i, sizes=(N,)) for i in range(count)]
+def default_instances(count, N, seed0, workers=None):
+    """Rough-surface batch-workload instances at one grid size (height maps included)."""
+    heights, insts = inputs.batch_heights(count, N, seed0, workers)
+    for b, inst in enumerate(insts):
+        inst["height"] = heights[b]
+    return insts

@@ -151,6 +151,16 @@ def test_argument_errors_before_any_device_call(bemlib):
         with pytest.raises(bem.BemError, match=msg) as e:
             bem.bem_make_kernel_layers(16, 0.1, layers, 1.0, 0.3)
         assert e.value.status == bem.BEM_EINVAL
+    # the open-plane operator is built for a homogeneous half-space only
+    with pytest.raises(bem.BemError, match="homogeneous") as e:
+        bem.bem_make_kernel(16, 0.1, 0.3, 4.0, 0.3, 1.0, 0.3, op_kind=bem.BEM_OP_OPEN)
+    assert e.value.status == bem.BEM_EUNSUPPORTED
+    with pytest.raises(bem.BemError, match="homogeneous") as e:
+        bem.bem_make_kernel_layers(16, 0.1, [(0.3, 4.0, 0.3)], 1.0, 0.3, op_kind=bem.BEM_OP_OPEN)
+    assert e.value.status == bem.BEM_EUNSUPPORTED
+    with pytest.raises(bem.BemError, match="op_kind") as e:
+        bem.bem_make_kernel(16, 0.1, 0.3, 4.0, 0.3, 1.0, 0.3, op_kind=7)
+    assert e.value.status == bem.BEM_EINVAL
     # batch: an empty batch is a no-op; a negative count is rejected with a message
     st, res = bem.bem_solve_batch([], [], [])
     assert st == bem.BEM_OK and res == []

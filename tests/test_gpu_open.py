@@ -50,7 +50,11 @@ def test_open_product_parity(cuda, N):
     ref = influence.matvec_dense_np(G, p) if N <= 16 else influence.matvec_fft_np(G, p)
     with open_kernel(N, delta, E, nu) as k:
         u = k.matvec(torch.tensor(p, device=cuda)).cpu().numpy()
-    assert rel(u, ref) < 1e-12
+    # The closed form of the cell coefficients is a sum of four terms of size about
+    # L log(L/delta) whose result falls like delta^2 / r: at the far offsets both sides
+    # (CUDA's and numpy's asinh) lose ~log10((L/delta)^2) digits to that cancellation,
+    # which leaves ~1e-12 on the product at N = 256 besides the FFT's rounding.
+    assert rel(u, ref) < 5e-12
     with open_kernel(N, delta, E, nu, "fp32") as k:
         u32 = k.matvec(torch.tensor(p, device=cuda, dtype=torch.float32)).double().cpu().numpy()
     assert rel(u32, ref) < 2e-6
