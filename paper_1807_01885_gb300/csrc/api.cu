@@ -149,8 +149,6 @@ void free_ws(bem_kernel_s* k) {
   cudaFree(w.twr);
   cudaFree(w.twc);
   cudaFree(w.twpc);
-  cudaFree(w.twpr);
-  cudaFree(w.rb4);
   cudaFree(w.vec);
   cudaFree(w.mask);
   cudaFree(w.partials);
@@ -440,11 +438,6 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
   if (k->prec == BEM_FP32 &&
       (e = cudaMalloc(&w.twpc, (size_t)pair_tw_count(k->logN + 1) * 4 * sizeof(float))) != cudaSuccess)
     return fail(e, "cudaMalloc(twpc)");
-  if (k->prec == BEM_FP32 &&
-      (e = cudaMalloc(&w.twpr, (size_t)pair_tw_count(k->logN) * 4 * sizeof(float))) != cudaSuccess)
-    return fail(e, "cudaMalloc(twpr)");
-  if (k->prec == BEM_FP32 && (e = cudaMalloc(&w.rb4, (size_t)(k->N + 1) * 4 * sizeof(float))) != cudaSuccess)
-    return fail(e, "cudaMalloc(rb4)");
   if ((e = cudaMalloc(&w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
   if ((e = cudaMalloc((void**)&w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
   if ((e = cudaMalloc((void**)&w.partials, 16 * 2048 * sizeof(double))) != cudaSuccess)

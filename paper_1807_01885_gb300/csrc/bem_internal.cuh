@@ -24,6 +24,28 @@ __host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_fl
 __host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+// float: the real and imaginary parts added by one packed two-wide instruction
+// (.f32x2, sm_100 family): half the issue slots of the FFT butterflies' additions
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -101,8 +123,6 @@ struct Workspace {
   void* twr = nullptr;       // stage twiddles of the length-N register FFT (rows)
   void* twc = nullptr;       // stage twiddles of the length-2N register FFT (columns)
   void* twpc = nullptr;      // float path: broadcast stage twiddles of the paired column FFT (4N float4)
-  void* twpr = nullptr;      // float path: the same for the paired row FFT (2N float4)
-  void* rb4 = nullptr;       // float path: broadcast e^{-i pi j/N}, j in [0, N] (N + 1 float4)
   void* vec = nullptr;       // solver vectors: p, g, t, r, u, f, x (N*N each)
   uint8_t* mask = nullptr;   // N*N contact mask (adhesive), plus a second copy; PK: contact set {p > 0}
   double* partials = nullptr;// per-block partial sums

@@ -252,180 +252,6 @@ k_col_r(cplx<T>* __restrict__ spec, const T* __restrict__ table, const cplx<T>* 
   }
 }
 
-// ---- float row passes on row pairs (fft_pair.cuh) ---------------------------------
-// Rows 2 pl and 2 pl + 1 of a block (pl < PPB pairs) are transformed together as one
-// packed length-N FFT of the pair; the spectrum goes to and comes from the
-// column-pair layout of the column pass (spec4[jp N + r] = (re_2jp, re_2jp+1,
-// im_2jp, im_2jp+1) of row r).  rb4[j] = e^{-i pi j / N} in broadcast form, j in [0, N].
-template <int LOGR> struct RowPairCfg { static constexpr int MAXT = 256, MINB = 2; };
-template <> struct RowPairCfg<3> { static constexpr int MAXT = 512, MINB = 1; };
-
-// row pairs per block
-template <int LOGN, int LOGR>
-__host__ __device__ constexpr int row_pairs_per_block() {
-  constexpr int c = RowPairCfg<LOGR>::MAXT / Plan<LOGN, LOGR>::T;
-  return c < 1 ? 1 : (c > (1 << (LOGN - 1)) ? (1 << (LOGN - 1)) : c);
-}
-// CP slots of one pair's shared buffer: the padded exchange buffer plus 9; it also
-// holds the pair's two rows of (N/2 + 1) spectrum records in the inverse pass.  The
-// odd count puts the buffers of neighbouring pairs in different 16-byte bank groups
-// (the forward pass's recombination reads the same index from two buffers at once).
-template <int LOGN, int LOGR>
-__host__ __device__ constexpr int row_pair_sh() {
-  return Plan<LOGN, LOGR>::PADL + 9;
-}
-
-template <int LOGN, int LOGR>
-__global__ void __launch_bounds__(RowPairCfg<LOGR>::MAXT, RowPairCfg<LOGR>::MINB)
-k_row_fwd_p(const float* __restrict__ p, float4* __restrict__ spec4, const float4* __restrict__ twpr,
-            const float4* __restrict__ rb4, const int* __restrict__ skip) {
-  using P = Plan<LOGN, LOGR>;
-  using pr::CP;
-  constexpr int N = 1 << LOGN, TT = P::T, SH = row_pair_sh<LOGN, LOGR>(), R = P::R;
-  constexpr int PPB = row_pairs_per_block<LOGN, LOGR>();
-  if (skip != nullptr && *skip == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CP* const sh0 = reinterpret_cast<CP*>(smem_raw);
-  const int pl = threadIdx.x / TT, t = threadIdx.x - pl * TT;
-  const int r0 = blockIdx.x * 2 * PPB;
-  CP* sh = sh0 + pl * SH;
-  CP v[R];
-  // row r packs its N reals as N/2 complex z[m] = (p[2m], p[2m + 1]), zero padded to N
-  const float2* pa = reinterpret_cast<const float2*>(p + (size_t)(r0 + 2 * pl) * N);
-  const float2* pb = pa + N / 2;
-#pragma unroll
-  for (int q = 0; q < R / 2; ++q) v[q] = pr::cp_make(pa[t + TT * q], pb[t + TT * q]);
-#pragma unroll
-  for (int q = R / 2; q < R; ++q) v[q] = pr::cp_zero();
-  pr::pair_fft<LOGN, LOGR, false, true, PPB>(v, sh, twpr, t, pl);
-#pragma unroll
-  for (int q = 0; q < R; ++q) sh[padi<LOGR>(t + TT * q)] = v[q];
-  __syncthreads();
-  // X[j] = (Z[j] + Z*[N-j])/2 - (i/2) e^{-i pi j/N} (Z[j] - Z*[N-j]) for both rows;
-  // thread (j0, pl2) forms X[j], X[j+1], j = 2 j0 + TT k (k even), of the pair pl2
-  const int j0 = threadIdx.x / PPB, pl2 = threadIdx.x - j0 * PPB;
-  const CP* shr = sh0 + pl2 * SH;
-  float4* outa = spec4 + r0 + 2 * pl2;
-  const pr::f2x half = pr::cpair(0.5f);
-#pragma unroll
-  for (int k = 0; k < R; k += 2) {
-    const int j = 2 * j0 + TT * k;
-    CP X2[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int jj = j + e;
-      const CP za = shr[padi<LOGR>(jj)];
-      const CP zr = shr[padi<LOGR>((N - jj) & (N - 1))];
-      // E = (za + conj zr)/2, D = (za - conj zr)/2, O = -i D
-      const CP E = CP{pr::mul2(pr::add2(za.re, zr.re), half), pr::mul2(pr::sub2(za.im, zr.im), half)};
-      const CP O = CP{pr::mul2(pr::add2(za.im, zr.im), half), pr::mul2(pr::sub2(zr.re, za.re), half)};
-      X2[e] = pr::cadd(E, pr::twmul<false>(O, pr::tw_load(rb4 + jj)));
-    }
-    float a0, b0, a1, b1, c0, d0, c1, d1;
-    pr::up2(X2[0].re, a0, b0);
-    pr::up2(X2[1].re, a1, b1);
-    pr::up2(X2[0].im, c0, d0);
-    pr::up2(X2[1].im, c1, d1);
-    const size_t o = (size_t)(j / 2) * N;
-    outa[o] = make_float4(a0, a1, c0, c1);
-    outa[o + 1] = make_float4(b0, b1, d0, d1);
-  }
-  if (j0 == 0) {
-    // pair N/2: X[N] = Re Z[0] - Im Z[0] and the empty column N + 1
-    const CP z0 = shr[0];
-    float a, b;
-    pr::up2(pr::sub2(z0.re, z0.im), a, b);
-    outa[(size_t)(N / 2) * N] = make_float4(a, 0.f, 0.f, 0.f);
-    outa[(size_t)(N / 2) * N + 1] = make_float4(b, 0.f, 0.f, 0.f);
-  }
-}
-
-template <int LOGN, int LOGR>
-__global__ void __launch_bounds__(RowPairCfg<LOGR>::MAXT, RowPairCfg<LOGR>::MINB)
-k_row_inv_p(const float4* __restrict__ spec4, float* __restrict__ u, const float4* __restrict__ twpr,
-            const float4* __restrict__ rb4, const int* __restrict__ skip) {
-  using P = Plan<LOGN, LOGR>;
-  using pr::CP;
-  constexpr int N = 1 << LOGN, TT = P::T, SH = row_pair_sh<LOGN, LOGR>(), R = P::R;
-  constexpr int PPB = row_pairs_per_block<LOGN, LOGR>(), NT = PPB * TT, NP = N / 2 + 1;
-  if (skip != nullptr && *skip == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CP* const sh0 = reinterpret_cast<CP*>(smem_raw);
-  const int pl = threadIdx.x / TT, t = threadIdx.x - pl * TT;
-  const int r0 = blockIdx.x * 2 * PPB;
-  CP* sh = sh0 + pl * SH;
-  // the block's 2 PPB rows of spectrum records: row 2 pl2 + e of the block goes to
-  // pair pl2's buffer at records [e NP, (e + 1) NP)
-  const float4* in4 = spec4 + r0;
-#pragma unroll
-  for (int k = 0; k < (2 * PPB * NP + NT - 1) / NT; ++k) {
-    const int e = threadIdx.x + NT * k;
-    if (e < 2 * PPB * NP) {
-      const int jp = e / (2 * PPB), rr = e - jp * (2 * PPB);
-      cp_async_elem(reinterpret_cast<float4*>(sh0 + (rr >> 1) * SH) + (rr & 1) * NP + jp, in4 + (size_t)jp * N + rr);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // Zi[j] = (Y[j] + Y*[N-j]) + i e^{+i pi j/N} (Y[j] - Y*[N-j]) for both rows.
-  // Thread t forms the frequency pairs jp = t + TT q (q < R/2), j = 2 jp and 2 jp + 1,
-  // from the records jp of both rows and their mirrors: N - 2 jp lies in record
-  // N/2 - jp (first of its two frequencies), N - 2 jp - 1 in record N/2 - jp - 1
-  // (second).  The values then go through the buffer to the FFT's input layout.
-  const float4* ra = reinterpret_cast<const float4*>(sh);
-  const float4* rbk = ra + NP;
-  CP v[R];
-  auto recomb = [&](CP y1, CP y2, int j) -> CP {
-    // e = y1 + conj y2, d = y1 - conj y2; Zi = e + i conj(w) d with w = e^{-i pi j/N}
-    const CP ev = CP{pr::add2(y1.re, y2.re), pr::sub2(y1.im, y2.im)};
-    const CP d = CP{pr::sub2(y1.re, y2.re), pr::add2(y1.im, y2.im)};
-    const CP dw = pr::twmul<true>(d, pr::tw_load(rb4 + j));
-    return CP{pr::sub2(ev.re, dw.im), pr::add2(ev.im, dw.re)};
-  };
-#pragma unroll
-  for (int q = 0; q < R / 2; ++q) {
-    const int jp = t + TT * q;
-    const float4 a = ra[jp], b = rbk[jp];
-    const float4 am = ra[N / 2 - jp], bm = rbk[N / 2 - jp];
-    const float4 an = ra[N / 2 - jp - 1], bn = rbk[N / 2 - jp - 1];
-    v[2 * q] = recomb(CP{pr::pk2(a.x, b.x), pr::pk2(a.z, b.z)}, CP{pr::pk2(am.x, bm.x), pr::pk2(am.z, bm.z)}, 2 * jp);
-    v[2 * q + 1] = recomb(CP{pr::pk2(a.y, b.y), pr::pk2(a.w, b.w)}, CP{pr::pk2(an.y, bn.y), pr::pk2(an.w, bn.w)},
-                          2 * jp + 1);
-  }
-  GroupSync<TT, PPB>::sync(pl);   // every record of the pair read
-#pragma unroll
-  for (int q = 0; q < R / 2; ++q) {
-    const int jp = t + TT * q;
-    sh[padi<LOGR>(2 * jp)] = v[2 * q];
-    sh[padi<LOGR>(2 * jp + 1)] = v[2 * q + 1];
-  }
-  GroupSync<TT, PPB>::sync(pl);
-#pragma unroll
-  for (int q = 0; q < R; ++q) v[q] = sh[padi<LOGR>(t + TT * q)];
-  GroupSync<TT, PPB>::sync(pl);   // read before the FFT's first exchange overwrites
-  pr::pair_fft<LOGN, LOGR, true, false, PPB>(v, sh, twpr, t, pl);
-  // z[m] = u[2m] + i u[2m+1] of each row, first N/2 values
-  float2* ua = reinterpret_cast<float2*>(u + (size_t)(r0 + 2 * pl) * N);
-  float2* ub = ua + N / 2;
-#pragma unroll
-  for (int q = 0; q < R / 2; ++q) {
-    float a, b, c, d;
-    pr::up2(v[q].re, a, b);
-    pr::up2(v[q].im, c, d);
-    ua[t + TT * q] = make_float2(a, c);
-    ub[t + TT * q] = make_float2(b, d);
-  }
-}
-
-// broadcast recombination twiddles rb4[j] = e^{-i pi j / N}, j in [0, N]
-static __global__ void k_recomb_bcast(float4* __restrict__ out, int N) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= N; j += gridDim.x * blockDim.x) {
-    double sn, cs;
-    sincospi((double)j / (double)N, &sn, &cs);
-    out[j] = make_float4((float)cs, (float)cs, (float)(-sn), (float)(-sn));
-  }
-}
-
 // Float column pass on column pairs: block c-slot handles the frequency columns 2 pr
 // and 2 pr + 1 (pr < npairs = N/2 + 1; the second column of the last pair is the
 // empty column N + 1, whose compliance is 0) as one packed transform (fft_pair.cuh):
@@ -544,33 +370,15 @@ struct RowLaunch {
   static void prepare() {
     static std::atomic<unsigned long long> attr{0};
     if (first_on_device(attr)) {
-      if constexpr (sizeof(T) == 4) {
-        cudaFuncSetAttribute(k_row_fwd_p<LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_row_inv_p<LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      } else {
-        cudaFuncSetAttribute(k_row_fwd_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_row_inv_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      }
+      cudaFuncSetAttribute(k_row_fwd_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_row_inv_r<T, LOGN, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }
   }
   static void pass(const bem_kernel_s* k, int which, const T* p, T* u, cudaStream_t s, const int* skip) {
     prepare();
     constexpr int N = 1 << LOGN;
     using PR = Plan<LOGN, LOGR>;
-    if constexpr (sizeof(T) == 4) {
-      constexpr int ppb = row_pairs_per_block<LOGN, LOGR>();
-      const size_t smem = (size_t)ppb * row_pair_sh<LOGN, LOGR>() * sizeof(pr::CP);
-      const int grid = N / (2 * ppb);
-      if (which == 0)
-        k_row_fwd_p<LOGN, LOGR><<<grid, ppb * PR::T, smem, s>>>((const float*)p, (float4*)k->ws.spec,
-                                                               (const float4*)k->ws.twpr, (const float4*)k->ws.rb4,
-                                                               skip);
-      else
-        k_row_inv_p<LOGN, LOGR><<<grid, ppb * PR::T, smem, s>>>((const float4*)k->ws.spec, (float*)u,
-                                                               (const float4*)k->ws.twpr, (const float4*)k->ws.rb4,
-                                                               skip);
-      return;
-    }
+
     constexpr int rpb = rows_per_block<T, LOGN, LOGR>();
     const size_t smem = (size_t)rpb * row_sh<LOGN, LOGR>() * sizeof(C);
     C* spec = (C*)k->ws.spec;
@@ -678,14 +486,11 @@ void reg_prepare(const bem_kernel_s* k) {
 
 template <typename T>
 void reg_twiddles(const bem_kernel_s* k, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4) {
-    k_stage_twiddles_pair<<<64, 256, 0, s>>>((float4*)k->ws.twpr, k->logN, row_logr<T>(k));
+  k_stage_twiddles<T><<<64, 256, 0, s>>>((cplx<T>*)k->ws.twr, k->logN, row_logr<T>(k));
+  if constexpr (sizeof(T) == 4)
     k_stage_twiddles_pair<<<64, 256, 0, s>>>((float4*)k->ws.twpc, k->logN + 1, col_logr<T>(k));
-    k_recomb_bcast<<<16, 256, 0, s>>>((float4*)k->ws.rb4, k->N);
-  } else {
-    k_stage_twiddles<T><<<64, 256, 0, s>>>((cplx<T>*)k->ws.twr, k->logN, row_logr<T>(k));
+  else
     k_stage_twiddles<T><<<64, 256, 0, s>>>((cplx<T>*)k->ws.twc, k->logN + 1, col_logr<T>(k));
-  }
 }
 
 }  // namespace bem

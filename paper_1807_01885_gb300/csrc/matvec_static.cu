@@ -28,7 +28,7 @@ constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Byte layout of the scratch for a grid of N cells per side (float path).
 struct StaticLayout {
-  size_t spec, table64, table, tw, twr, twc, twpc, twpr, rb4, total;
+  size_t spec, table64, table, tw, twr, twc, twpc, total;
   explicit StaticLayout(int N) {
     const size_t c = 2 * sizeof(float);
     const size_t blocked = (size_t)(N / TC + 1) * (N + 1) * TC, square = (size_t)(N + 1) * (N + 4);
@@ -47,10 +47,6 @@ struct StaticLayout {
     off += round256((size_t)4 * N * c);
     twpc = off;
     off += round256((size_t)4 * N * 4 * sizeof(float));
-    twpr = off;
-    off += round256((size_t)2 * N * 4 * sizeof(float));
-    rb4 = off;
-    off += round256((size_t)(N + 1) * 4 * sizeof(float));
     total = off;
   }
 };
@@ -155,8 +151,6 @@ extern "C" bem_status bem_matvec_static(const bem_kernel_desc* desc, const float
   k.ws.twr = b + lay.twr;
   k.ws.twc = b + lay.twc;
   k.ws.twpc = b + lay.twpc;
-  k.ws.twpr = b + lay.twpr;
-  k.ws.rb4 = b + lay.rb4;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   st = build_table(&k, s);
   if (st != BEM_OK) return st;
