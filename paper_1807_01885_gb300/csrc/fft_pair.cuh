@@ -249,12 +249,6 @@ __host__ __device__ constexpr int twp_offset(int s) {
   return off;
 }
 
-// records of all stage tables of a length-2^LOGL plan
-template <int LOGL, int LOGR>
-__host__ __device__ constexpr int twp_total() {
-  return twp_offset<LOGL, LOGR>(Plan<LOGL, LOGR>::NSTAGES);
-}
-
 // x(r) *= w_r (conjugated for INV), r = 1..Q-1, for one k of a stage whose planes
 // start at tws (ns records per plane)
 template <int Q, bool INV, typename X>

@@ -232,6 +232,170 @@ __global__ void k_twiddle_mats(const float2* __restrict__ tw, float* __restrict_
   }
 }
 
+// ---- truncated transforms along y on the tensor cores ----------------------------
+// Both y-transforms are matrix products with a dimension of 2m (= n2m) on one side:
+// forward C (rows x n2m) = V (rows x N) Tf (N x n2m), inverse out (rows x N) =
+// (A diag(cs)) (rows x n2m) Ti (n2m x N).  They run as mma.sync m16n8k16 with bf16
+// operands and float accumulation.  A bf16 value keeps 8 significant bits, so every
+// float operand x is split into hi = bf16(x) and lo = bf16(x - hi) (together 16 bits,
+// |x - hi - lo| <= 2^-18 |x|), and a product takes the three terms hi.hi, hi.lo, lo.hi
+// (the dropped lo.lo is below 2^-18 of it): float-level products from bf16 inputs.
+// The constant operand (Tf or Ti) is stored split and in fragment order: for k-block
+// kb (16 k) and n-tile nt (8 columns), lane l holds uint4 (hi b0, hi b1, lo b0, lo b1)
+// with b0 = (B[16 kb + 2t][8 nt + g], B[16 kb + 2t + 1][.]), b1 = the same 8 k further,
+// g = l / 4, t = l % 4 (the m16n8k16 B layout); entries outside the matrix are 0.
+__device__ __forceinline__ unsigned pack_bf16x2(float lo_elem, float hi_elem) {
+  unsigned d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
+  return d;
+}
+__device__ __forceinline__ float bf16_lo_f(unsigned v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi_f(unsigned v) { return __uint_as_float(v & 0xffff0000u); }
+// (x0, x1) -> hi and lo bf16 pairs, x0 in the lower half
+__device__ __forceinline__ void split2(float x0, float x1, unsigned& hi, unsigned& lo) {
+  hi = pack_bf16x2(x0, x1);
+  lo = pack_bf16x2(x0 - bf16_lo_f(hi), x1 - bf16_hi_f(hi));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// hi.hi + hi.lo + lo.hi
+__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4], uint4 b) {
+  mma_bf16(d, ah, b.x, b.y);
+  mma_bf16(d, ah, b.z, b.w);
+  mma_bf16(d, al, b.x, b.y);
+}
+
+// fragment-ordered split copy of B (K x Ncols, element (k, n) at Bm[k ldk + n ldn])
+__global__ void k_frag_b(const float* __restrict__ Bm, int K, int Nc, size_t ldk, size_t ldn, uint4* __restrict__ out) {
+  const int KT = (K + 15) / 16, NT = (Nc + 7) / 8;
+  FOR_N(i, (size_t)KT * NT * 32) {
+    const int lane = (int)(i % 32), nt = (int)((i / 32) % NT), kb = (int)(i / (32 * (size_t)NT));
+    const int g = lane / 4, t = lane % 4, n = 8 * nt + g;
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = 16 * kb + 2 * t + (e & 1) + 8 * (e >> 1);
+      v[e] = (k < K && n < Nc) ? Bm[(size_t)k * ldk + (size_t)n * ldn] : 0.f;
+    }
+    unsigned h0, l0, h1, l1;
+    split2(v[0], v[1], h0, l0);
+    split2(v[2], v[3], h1, l1);
+    out[i] = make_uint4(h0, h1, l0, l1);
+  }
+}
+
+constexpr int TC_NT_MAX = 8;   // n2m <= 64 (modes <= 32) on the tensor-core path
+
+// C[r][j] = sum_y V[r][y] Tf[y][j]: one warp per 16 rows, every n-tile of n2m
+__global__ void __launch_bounds__(128) k_dft_y_tc(const float* __restrict__ V, const uint4* __restrict__ TfB,
+                                                  float* __restrict__ C, size_t rows, int N, int n2m) {
+  const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
+  const size_t R0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * 16;
+  if (R0 >= rows) return;
+  const int KT = (N + 15) / 16, NT = (n2m + 7) / 8;
+  float acc[TC_NT_MAX][4];
+#pragma unroll
+  for (int nt = 0; nt < TC_NT_MAX; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+  const size_t ra = R0 + g, rb = R0 + g + 8;
+  const float* va = V + ra * N;
+  const float* vb = V + rb * N;
+  const bool oka = ra < rows, okb = rb < rows;
+  for (int kb = 0; kb < KT; ++kb) {
+    const int k0 = 16 * kb + 2 * t, k1 = k0 + 8;
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 x0 = (oka && k0 < N) ? *reinterpret_cast<const float2*>(va + k0) : z;
+    const float2 x1 = (okb && k0 < N) ? *reinterpret_cast<const float2*>(vb + k0) : z;
+    const float2 x2 = (oka && k1 < N) ? *reinterpret_cast<const float2*>(va + k1) : z;
+    const float2 x3 = (okb && k1 < N) ? *reinterpret_cast<const float2*>(vb + k1) : z;
+    unsigned ah[4], al[4];
+    split2(x0.x, x0.y, ah[0], al[0]);
+    split2(x1.x, x1.y, ah[1], al[1]);
+    split2(x2.x, x2.y, ah[2], al[2]);
+    split2(x3.x, x3.y, ah[3], al[3]);
+    const uint4* bk = TfB + (size_t)kb * NT * 32 + lane;
+#pragma unroll
+    for (int nt = 0; nt < TC_NT_MAX; ++nt)
+      if (nt < NT) mma3(acc[nt], ah, al, bk[nt * 32]);
+  }
+#pragma unroll
+  for (int nt = 0; nt < TC_NT_MAX; ++nt) {
+    const int col = 8 * nt + 2 * t;
+    if (nt < NT && col < n2m) {
+      if (oka) *reinterpret_cast<float2*>(C + ra * n2m + col) = make_float2(acc[nt][0], acc[nt][1]);
+      if (okb) *reinterpret_cast<float2*>(C + rb * n2m + col) = make_float2(acc[nt][2], acc[nt][3]);
+    }
+  }
+}
+
+// out[r][y] (+)= sum_k A[r][k] cs(k) Ti[k][y], cs(k) = scale (c ? c[k/2] : 1): one
+// warp per 16 rows and 64 columns (8 n-tiles), the scaled A split once per warp
+constexpr int TC_IY = 64;
+template <bool ACCUM>
+__global__ void __launch_bounds__(128) k_idft_y_tc(const float* __restrict__ A, const uint4* __restrict__ TiB,
+                                                   const float* __restrict__ c, float scale, float* __restrict__ out,
+                                                   size_t rows, int N, int n2m) {
+  const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
+  const size_t R0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * 16;
+  if (R0 >= rows) return;
+  const int y0 = blockIdx.y * TC_IY;
+  const int KT = (n2m + 15) / 16, NT = (N + 7) / 8;
+  const size_t ra = R0 + g, rb = R0 + g + 8;
+  const bool oka = ra < rows, okb = rb < rows;
+  unsigned ah[4][4], al[4][4];   // k-blocks (n2m <= 64)
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb) {
+    const int k0 = 16 * kb + 2 * t, k1 = k0 + 8;
+    auto ld = [&](bool ok, size_t r, int k) -> float2 {
+      if (!ok || k >= n2m) return make_float2(0.f, 0.f);
+      const float2 v = *reinterpret_cast<const float2*>(A + r * n2m + k);
+      const float s0 = scale * (c != nullptr ? c[k / 2] : 1.f), s1 = scale * (c != nullptr ? c[(k + 1) / 2] : 1.f);
+      return make_float2(v.x * s0, v.y * s1);
+    };
+    float2 x0 = make_float2(0.f, 0.f), x1 = x0, x2 = x0, x3 = x0;
+    if (kb < KT) {
+      x0 = ld(oka, ra, k0);
+      x1 = ld(okb, rb, k0);
+      x2 = ld(oka, ra, k1);
+      x3 = ld(okb, rb, k1);
+    }
+    split2(x0.x, x0.y, ah[kb][0], al[kb][0]);
+    split2(x1.x, x1.y, ah[kb][1], al[kb][1]);
+    split2(x2.x, x2.y, ah[kb][2], al[kb][2]);
+    split2(x3.x, x3.y, ah[kb][3], al[kb][3]);
+  }
+#pragma unroll
+  for (int j = 0; j < TC_IY / 8; ++j) {
+    const int nt = y0 / 8 + j;
+    if (nt >= NT) break;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb)
+      if (kb < KT) mma3(acc, ah[kb], al[kb], TiB[((size_t)kb * NT + nt) * 32 + lane]);
+    const int y = 8 * nt + 2 * t;
+    if (y < N) {
+      if (oka) {
+        float2* o = reinterpret_cast<float2*>(out + ra * N + y);
+        float2 v = make_float2(acc[0], acc[1]);
+        if (ACCUM) { const float2 w = *o; v.x += w.x; v.y += w.y; }
+        *o = v;
+      }
+      if (okb) {
+        float2* o = reinterpret_cast<float2*>(out + rb * N + y);
+        float2 v = make_float2(acc[2], acc[3]);
+        if (ACCUM) { const float2 w = *o; v.x += w.x; v.y += w.y; }
+        *o = v;
+      }
+    }
+  }
+}
+
 // c_k / N^2, the weights of the gradient of the inverse transform, for the current N
 __global__ void k_cky_scaled(const float* __restrict__ c, float* __restrict__ cs, int m, float inv) {
   FOR_N(k, (size_t)m) cs[k] = c[k] * inv;
@@ -544,6 +708,7 @@ struct bem_fno_s {
   double* mom_part = nullptr;   // per-chunk sums of the height moments
   float2 *A = nullptr, *Y = nullptr, *dY = nullptr, *tw = nullptr;
   float *Tf = nullptr, *Ti = nullptr;   // twiddle matrices of the y transforms (N x 2m, 2m x N)
+  uint4 *TfB = nullptr, *TiB = nullptr; // the same split into bf16 hi/lo, in mma fragment order
   double* lpart = nullptr;
   std::vector<void*> owned;
   size_t n_persistent = 0;   // leading entries of owned that live as long as the handle
@@ -557,6 +722,9 @@ cudaError_t alloc(bem_fno_s* f, P** p, size_t count) {
   if (e == cudaSuccess) f->owned.push_back(*p);
   return e;
 }
+
+// the tensor-core y transforms hold up to 8 n-tiles of 2m columns (m <= 32)
+bool tc_ok(const bem_fno_s* f) { return 2 * f->d.modes <= 8 * TC_NT_MAX; }
 
 constexpr int kMaxSamples = 4096;
 // frees the activation buffers: everything allocated after the handle's persistent
@@ -577,6 +745,13 @@ void set_twiddles(bem_fno_s* f, int N, cudaStream_t s) {
   k_twiddle_mats<<<blocks_for((size_t)N * m), FT, 0, s>>>(f->tw, f->Tf, f->Ti, N, m);
   k_cky_scaled<<<1, 32, 0, s>>>(f->cky, f->cky_s, m, (float)(1.0 / ((double)N * N)));
   note_launches(3);
+  if (tc_ok(f)) {
+    const int n2m = 2 * m;
+    // forward B = Tf (K = N, columns n2m), inverse B = Ti (K = n2m, columns N)
+    k_frag_b<<<blocks_for((size_t)((N + 15) / 16) * ((n2m + 7) / 8) * 32), FT, 0, s>>>(f->Tf, N, n2m, n2m, 1, f->TfB);
+    k_frag_b<<<blocks_for((size_t)((n2m + 15) / 16) * ((N + 7) / 8) * 32), FT, 0, s>>>(f->Ti, n2m, N, N, 1, f->TiB);
+    note_launches(2);
+  }
   f->twN = N;
 }
 
@@ -611,6 +786,10 @@ bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
   if (e == cudaSuccess) e = alloc(f, &f->tw, (size_t)N);
   if (e == cudaSuccess) e = alloc(f, &f->Tf, (size_t)2 * m * N);
   if (e == cudaSuccess) e = alloc(f, &f->Ti, (size_t)2 * m * N);
+  if (e == cudaSuccess && tc_ok(f))
+    e = alloc(f, &f->TfB, (size_t)((N + 15) / 16) * ((2 * m + 7) / 8) * 32);
+  if (e == cudaSuccess && tc_ok(f))
+    e = alloc(f, &f->TiB, (size_t)((2 * m + 15) / 16) * ((N + 7) / 8) * 32);
   const size_t nblk = (size_t)B * ((P + FT - 1) / FT);
   const size_t maxout = (size_t)std::max(W, H) * std::max({W, H, 7}) + std::max(W, H);
   if (e == cudaSuccess && train) e = alloc(f, &f->part, nblk * maxout);
@@ -668,6 +847,10 @@ void wgrad(const float* dY, int cout, const float* X, int cin, float* gw, float*
 // A (rows x m complex) = truncated DFT along y of the rows of v
 void dft_y(bem_fno_s* f, const float* v, size_t rows, int N, cudaStream_t s) {
   const int n2m = 2 * f->d.modes;
+  if (tc_ok(f)) {
+    k_dft_y_tc<<<(unsigned)((rows + 63) / 64), 128, 0, s>>>(v, f->TfB, reinterpret_cast<float*>(f->A), rows, N, n2m);
+    return;
+  }
   const dim3 grid((unsigned)((rows + G1_BM - 1) / G1_BM), (unsigned)((n2m + G1_BN - 1) / G1_BN));
   k_dft_y_gemm<<<grid, 256, 0, s>>>(v, f->Tf, reinterpret_cast<float*>(f->A), rows, N, n2m);
 }
@@ -676,6 +859,11 @@ void dft_y(bem_fno_s* f, const float* v, size_t rows, int N, cudaStream_t s) {
 template <bool ACCUM>
 void idft_y(bem_fno_s* f, float* out, const float* c, float scale, size_t rows, int N, cudaStream_t s) {
   const int n2m = 2 * f->d.modes;
+  if (tc_ok(f)) {
+    const dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((N + TC_IY - 1) / TC_IY));
+    k_idft_y_tc<ACCUM><<<grid, 128, 0, s>>>(reinterpret_cast<const float*>(f->A), f->TiB, c, scale, out, rows, N, n2m);
+    return;
+  }
   const dim3 grid((unsigned)((rows + G2_BM - 1) / G2_BM), (unsigned)((N + G2_BN - 1) / G2_BN));
   k_idft_y_gemm<ACCUM><<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(f->A), f->Ti, c, scale, out, rows, N,
                                             n2m);

@@ -281,12 +281,8 @@ k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float
   const int pair = blockIdx.x * CPB + c;
   const bool active = pair < npairs;
   CP* sh = reinterpret_cast<CP*>(smem_raw) + c * SH;
-  // the stage twiddles (all stages, both transforms) and the block's compliance rows
-  // are copied to shared memory while the column data loads
-  constexpr int NTW = pr::twp_total<LOGM, LOGR>();
-  float4* twsh = reinterpret_cast<float4*>(reinterpret_cast<CP*>(smem_raw) + CPB * SH);
-  float2* ksh = reinterpret_cast<float2*>(twsh + NTW);
-  for (int e = threadIdx.x; e < NTW; e += CPB * TT) cp_async_elem(twsh + e, twp + e);
+  // the block's compliance rows, copied to shared memory while the forward FFT runs
+  float2* ksh = reinterpret_cast<float2*>(reinterpret_cast<CP*>(smem_raw) + CPB * SH);
   {
     const int pair0 = blockIdx.x * CPB;
     const int nact = min(CPB, npairs - pair0);
@@ -299,9 +295,9 @@ k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float
   for (int q = 0; q < R / 2; ++q) v[q] = active ? pr::cp_load(col + t + TT * q) : pr::cp_zero();
 #pragma unroll
   for (int q = R / 2; q < R; ++q) v[q] = pr::cp_zero();
+  pr::pair_fft<LOGM, LOGR, false, true, CPB>(v, sh, twp, t, c);
   cp_async_wait_all();
   __syncthreads();
-  pr::pair_fft<LOGM, LOGR, false, true, CPB>(v, sh, twsh, t, c);
   const float2* kt = ksh + c * (N + 1);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -310,7 +306,7 @@ k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float
     const float2 kv = active ? kt[f] : make_float2(0.f, 0.f);
     v[q] = pr::cscale2(v[q], pr::pk2(kv.x, kv.y));
   }
-  pr::pair_fft<LOGM, LOGR, true, false, CPB>(v, sh, twsh, t, c);
+  pr::pair_fft<LOGM, LOGR, true, false, CPB>(v, sh, twp, t, c);
   if (active) {
 #pragma unroll
     for (int q = 0; q < R / 2; ++q) pr::cp_store(col + t + TT * q, v[q]);
@@ -415,8 +411,7 @@ struct ColLaunch {
       constexpr int ppb = pairs_per_block<LOGN + 1, LOGR>();
       const int npairs = N / 2 + 1;
       const int grid = (npairs + ppb - 1) / ppb;
-      const size_t smem = (size_t)ppb * ((PC::PADL + 8) * sizeof(pr::CP) + (N + 1) * sizeof(float2)) +
-                          (size_t)pr::twp_total<LOGN + 1, LOGR>() * sizeof(float4);
+      const size_t smem = (size_t)ppb * ((PC::PADL + 8) * sizeof(pr::CP) + (N + 1) * sizeof(float2));
       k_col_p<LOGN + 1, LOGR><<<grid, ppb * PC::T, smem, s>>>((float4*)k->ws.spec, (const float2*)k->ws.table,
                                                              (const float4*)k->ws.twpc, npairs, skip);
     } else {

@@ -40,7 +40,7 @@ def setup(cuda, W, m, L, H, seed):
     return net, unflatten(rounded.cpu().numpy(), P)
 
 
-@pytest.mark.parametrize("W,m,L,H,B,N", [(8, 3, 2, 16, 2, 16), (32, 16, 4, 64, 1, 32)])
+@pytest.mark.parametrize("W,m,L,H,B,N", [(8, 3, 2, 16, 2, 16), (32, 16, 4, 64, 1, 32), (32, 16, 4, 64, 1, 256)])
 def test_forward_matches_oracle(cuda, W, m, L, H, B, N):
     net, P = setup(cuda, W, m, L, H, seed=W)
     rng = np.random.default_rng(1)
@@ -53,8 +53,8 @@ def test_forward_matches_oracle(cuda, W, m, L, H, B, N):
     net.close()
 
 
-def test_gradients_match_oracle(cuda):
-    W, m, L, H, B, N = 8, 3, 2, 16, 2, 16
+@pytest.mark.parametrize("W,m,L,H,B,N", [(8, 3, 2, 16, 2, 16), (16, 6, 2, 16, 2, 64)])
+def test_gradients_match_oracle(cuda, W, m, L, H, B, N):
     net, P = setup(cuda, W, m, L, H, seed=3)
     rng = np.random.default_rng(4)
     x = rng.standard_normal((B, 7, N, N)).astype(np.float32)
