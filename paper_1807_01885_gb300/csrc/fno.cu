@@ -396,6 +396,68 @@ __global__ void __launch_bounds__(128) k_idft_y_tc(const float* __restrict__ A, 
   }
 }
 
+// Pointwise (1x1) layer on the tensor cores: for 16 pixels of one sample (a warp)
+// D (pixels x cout) = X^T (pixels x cin) W^T (cin x cout), the activations split into
+// bf16 hi + lo (two mma.sync each), the weights used as they are stored (bf16).  Same
+// result as k_pw: Y[b][o][p] = bias[o] + sum_c W[o][c] X[b][c][p] (+ Y when ACCUM),
+// Yact = gelu(Y) when GELU; TRANS uses W^T.  KT = ceil(cin/16) k-blocks, NT =
+// ceil(cout/8) n-tiles (cout <= 64).
+template <int KT, int NT, bool TRANS, bool ACCUM, bool GELU>
+__global__ void __launch_bounds__(128) k_pw_tc(const float* __restrict__ X, int cin, const bf16* __restrict__ Wt,
+                                               const bf16* __restrict__ bias, float* __restrict__ Y,
+                                               float* __restrict__ Yact, int cout, size_t P) {
+  const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
+  const int b = blockIdx.y;
+  const size_t p0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * 16;
+  if (p0 >= P) return;
+  const size_t pa = p0 + g, pb = p0 + g + 8;
+  const bool oka = pa < P, okb = pb < P;
+  const float* xb = X + (size_t)b * cin * P;
+  auto xv = [&](int c, size_t p, bool ok) -> float { return (ok && c < cin) ? xb[(size_t)c * P + p] : 0.f; };
+  unsigned ah[KT][4], al[KT][4];
+#pragma unroll
+  for (int kb = 0; kb < KT; ++kb) {
+    const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
+    split2(xv(c0, pa, oka), xv(c0 + 1, pa, oka), ah[kb][0], al[kb][0]);
+    split2(xv(c0, pb, okb), xv(c0 + 1, pb, okb), ah[kb][1], al[kb][1]);
+    split2(xv(c1, pa, oka), xv(c1 + 1, pa, oka), ah[kb][2], al[kb][2]);
+    split2(xv(c1, pb, okb), xv(c1 + 1, pb, okb), ah[kb][3], al[kb][3]);
+  }
+  // B[c][o] = W[o][c]: TRANS reads Wt[c][o] (stored [cin][cout]), else Wt[o][c]
+  auto wbits = [&](int c, int o) -> unsigned {
+    if (c >= cin || o >= cout) return 0u;
+    const bf16 w = TRANS ? Wt[(size_t)c * cout + o] : Wt[(size_t)o * cin + c];
+    return (unsigned)__bfloat16_as_ushort(w);
+  };
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int n = 8 * nt + g;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kb = 0; kb < KT; ++kb) {
+      const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
+      const unsigned b0 = wbits(c0, n) | (wbits(c0 + 1, n) << 16);
+      const unsigned b1 = wbits(c1, n) | (wbits(c1 + 1, n) << 16);
+      mma_bf16(acc, ah[kb], b0, b1);
+      mma_bf16(acc, al[kb], b0, b1);
+    }
+    // acc[0], acc[1]: pixel pa, outputs o0, o0 + 1; acc[2], acc[3]: pixel pb
+    const int o0 = 8 * nt + 2 * t;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int o = o0 + (e & 1);
+      const size_t p = (e < 2) ? pa : pb;
+      const bool ok = (e < 2) ? oka : okb;
+      if (!ok || o >= cout) continue;
+      float v = acc[e] + (bias != nullptr ? b2f(bias[o]) : 0.f);
+      float* y = Y + ((size_t)b * cout + o) * P + p;
+      if (ACCUM) v += *y;
+      *y = v;
+      if (GELU) Yact[((size_t)b * cout + o) * P + p] = gelu_f(v);
+    }
+  }
+}
+
 // c_k / N^2, the weights of the gradient of the inverse transform, for the current N
 __global__ void k_cky_scaled(const float* __restrict__ c, float* __restrict__ cs, int m, float inv) {
   FOR_N(k, (size_t)m) cs[k] = c[k] * inv;
@@ -812,9 +874,35 @@ bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
 }
 
 // pointwise layer dispatch on the (compile-time) input width
+template <int KT, int NT, bool TRANS, bool ACCUM, bool GELU>
+void pw_tc_launch(const float* X, int cin, const bf16* Wt, const bf16* bias, float* Y, float* Yact, int cout,
+                  size_t P, int B, cudaStream_t s) {
+  const dim3 grid((unsigned)((P + 63) / 64), B);
+  k_pw_tc<KT, NT, TRANS, ACCUM, GELU><<<grid, 128, 0, s>>>(X, cin, Wt, bias, Y, Yact, cout, P);
+}
+
+template <int KT, bool TRANS, bool ACCUM, bool GELU>
+void pw_tc_nt(const float* X, int cin, const bf16* Wt, const bf16* bias, float* Y, float* Yact, int cout, size_t P,
+              int B, cudaStream_t s) {
+  switch ((cout + 7) / 8) {
+    case 1: pw_tc_launch<KT, 1, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s); break;
+    case 2: pw_tc_launch<KT, 2, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s); break;
+    case 4: pw_tc_launch<KT, 4, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s); break;
+    default: pw_tc_launch<KT, 8, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s); break;
+  }
+}
+
 template <bool TRANS, bool ACCUM, bool GELU>
 void pw(const float* X, int cin, const bf16* Wt, const bf16* bias, float* Y, float* Yact, int cout, size_t P, int B,
         cudaStream_t s) {
+  // the tensor-core form wherever a contraction has something to contract (cin >= 7)
+  if (cin >= 7 && cout <= 64) {
+    if (cin <= 16) pw_tc_nt<1, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s);
+    else if (cin <= 32) pw_tc_nt<2, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s);
+    else pw_tc_nt<4, TRANS, ACCUM, GELU>(X, cin, Wt, bias, Y, Yact, cout, P, B, s);
+    note_launches(1);
+    return;
+  }
   dim3 grid((unsigned)((P + FT - 1) / FT), B);
   const size_t sm = (size_t)cout * cin * sizeof(float);
   switch (cin) {
