@@ -249,7 +249,7 @@ PROFILE = os.path.join(ROOT, "profiles", "col_pass_N2048_fp32.md")
 # the sources of the three FFT passes (the column pass, its FFT and its launch);
 # a change to any of them invalidates the captured traffic
 PROFILED_SOURCES = ["paper_1807_01885_gb300/csrc/matvec_reg.cuh", "paper_1807_01885_gb300/csrc/fft_reg.cuh",
-                    "paper_1807_01885_gb300/csrc/matvec_f32.cu"]
+                    "paper_1807_01885_gb300/csrc/fft_pair.cuh", "paper_1807_01885_gb300/csrc/matvec_f32.cu"]
 
 
 def profiled_traffic():

@@ -10,6 +10,8 @@
 #include <vector>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bem_internal.cuh"
 
 namespace bem {
@@ -62,6 +64,12 @@ bem_status check_desc(const bem_kernel_desc* d) {
 }
 
 namespace {
+
+// NVTX range around an entry point (shown by Nsight tools; no cost when none attaches)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -465,6 +473,7 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
 }
 
 bem_status bem_make_kernel(const bem_kernel_desc* desc, void* cuda_stream, bem_kernel* out) {
+  Range range("bem_make_kernel");
   return make_kernel(desc, 0, nullptr, cuda_stream, out);
 }
 
@@ -525,6 +534,7 @@ bem_status bem_kernel_table(bem_kernel k, void* out, void* cuda_stream) {
 }
 
 bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream) {
+  Range range("bem_matvec");
   if (k == nullptr || p == nullptr || u == nullptr) { set_error("NULL argument"); return BEM_EINVAL; }
   DeviceGuard g(k->dev);
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -552,6 +562,7 @@ bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream) {
 
 bem_status bem_solve_contact(bem_kernel k, const bem_problem* prob, void* p_out, bem_result* res,
                              void* cuda_stream) {
+  Range range("bem_solve_contact");
   if (k == nullptr || res == nullptr) {
     set_error("NULL argument");
     return BEM_EINVAL;
@@ -598,6 +609,7 @@ bem_status bem_solve_contact(bem_kernel k, const bem_problem* prob, void* p_out,
 
 bem_status bem_solve_batch(int32_t n, const bem_kernel* kernels, const bem_problem* probs, void* const* p_out,
                            bem_result* res, void* cuda_stream) {
+  Range range("bem_solve_batch");
   if (n < 0 || (n > 0 && (kernels == nullptr || probs == nullptr || res == nullptr))) {
     set_error("invalid batch arguments");
     return BEM_EINVAL;

@@ -70,7 +70,7 @@ FIG5_ALPHAS = [0.1, 0.2, 0.5, 2.0, 15.0]
 FIG5_RESULTS = {}
 
 
-def _fig5_ramp(cuda, alpha, N=512):
+def _fig5_ramp(cuda, alpha, N=512, precision="fp64", tol=1e-9):
     E1, nu, h, dg = 1e9, 0.3, 2e-3, 100.0
     Es = okernel.e_star(E1, nu)
     R = alpha * np.sqrt(Es * h ** 3 / (2 * dg))
@@ -79,12 +79,13 @@ def _fig5_ramp(cuda, alpha, N=512):
     d_c, a_c, F_c = analytic.thin_layer_sphere_critical(R, h, E1, nu, dg)
     a_ref = min(a_F, a_c)                                        # the relevant limit's radius
     delta = 6 * a_ref / N
-    f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    f = torch.tensor(inputs.sphere_height(N, delta, R), device=cuda, dtype=dt)
     d_max = (1.5 * a_ref) ** 2 / R
     d_end = 1.3 * min(analytic.jkr_jump_off(R, Es, dg)[2], d_c)
     depths = ramp.depth_schedule(d_max, d_end, 8, 70)
-    with bem.Kernel(N, delta, h, E1, nu, np.inf, 0.3) as k:
-        out = ramp.run(k, f, depths, dg, tol=1e-9)
+    with bem.Kernel(N, delta, h, E1, nu, np.inf, 0.3, precision=precision) as k:
+        out = ramp.run(k, f, depths, dg, tol=tol)
     return out, R, h, E1, nu, dg, a_ref
 
 
@@ -101,6 +102,25 @@ def test_fig5_pull_off_force_between_limits(cuda, alpha):
         thick = np.min(analytic.thick_layer_sphere(a, R, h, E1, nu, dg)[0]) / (np.pi * R * dg)
         assert ratio / thick == pytest.approx(1.0, abs=0.04)
     if alpha >= 15:
+        assert ratio / -2.0 == pytest.approx(1.0, abs=0.06)
+
+
+@pytest.mark.parametrize("alpha", [0.2, 15.0])
+def test_fig5_float_path_at_n1024(cuda, alpha):
+    """The Fig. 5 sweep's two ends on the float path (FP32 vectors and FFTs, double
+    detachment test) at N = 1024 (pull-off contact radius about 170 cells): the same
+    bounds as the FP64 runs at N = 512 (between -3/2 and -2; the thick-layer expansion
+    within 4 % at alpha = 0.2, Eq. 19 within 6 % at alpha = 15)."""
+    out, R, h, E1, nu, dg, a_ref = _fig5_ramp(cuda, alpha, N=1024, precision="fp32", tol=1e-7)
+    assert all(r["status"] == 0 for r in out)
+    assert out[-1]["n_contact"] == 0
+    ratio = min(r["force"] for r in out) / (np.pi * R * dg)
+    assert -2.0 * 1.01 < ratio < -1.5 * 0.97
+    if alpha <= 0.2:
+        a = np.linspace(0.05, 2.5, 4000) * a_ref
+        thick = np.min(analytic.thick_layer_sphere(a, R, h, E1, nu, dg)[0]) / (np.pi * R * dg)
+        assert ratio / thick == pytest.approx(1.0, abs=0.04)
+    else:
         assert ratio / -2.0 == pytest.approx(1.0, abs=0.06)
 
 
