@@ -458,6 +458,228 @@ __global__ void __launch_bounds__(128) k_pw_tc(const float* __restrict__ X, int 
   }
 }
 
+// ---- fused Fourier layer (forward) --------------------------------------------
+// One kernel for z = W v + b + S(v) and v' = gelu(z): for 16 pixels y of one row x of
+// one sample, both contractions go into the same accumulator (pixels x cout):
+//   W v:  A = v^T (pixels x cin, split hi/lo), B = W^T (bf16 as stored),
+//   S(v): A = Tf (pixels y x 2m: the inverse y-transform's e^{+i k y} terms, which are
+//         the forward twiddles read as Re/Im pairs), B = (c_k / N^2) A_row (2m x cout:
+//         the x-inverse of the mixed modes of this row, split hi/lo), three products.
+// The inverse y-transform's output never goes to memory.  The pixel-operand Tf is
+// stored split and in A-fragment order (k_frag_a); the row operand is gathered once
+// per warp and row.
+// fragment-ordered split copy of A (M x K, element (r, k) at Am[r ldr + k]): for m-tile
+// mt and k-block kb, lane l holds uint4 hi (a0..a3) and uint4 lo (a0..a3) with a0 =
+// (A[16 mt + g][16 kb + 2t], A[.][+1]), a1 = row + 8, a2 = col + 8, a3 = both
+__global__ void k_frag_a(const float* __restrict__ Am, int M, int K, size_t ldr, uint4* __restrict__ out) {
+  const int MT = (M + 15) / 16, KB = (K + 15) / 16;
+  FOR_N(i, (size_t)MT * KB * 32) {
+    const int lane = (int)(i % 32), kb = (int)((i / 32) % KB), mt = (int)(i / (32 * (size_t)KB));
+    const int g = lane / 4, t = lane % 4;
+    unsigned h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 16 * mt + g + 8 * (e & 1), k = 16 * kb + 2 * t + 8 * (e >> 1);
+      const float x0 = (r < M && k < K) ? Am[(size_t)r * ldr + k] : 0.f;
+      const float x1 = (r < M && k + 1 < K) ? Am[(size_t)r * ldr + k + 1] : 0.f;
+      split2(x0, x1, h[e], l[e]);
+    }
+    out[2 * i] = make_uint4(h[0], h[1], h[2], h[3]);
+    out[2 * i + 1] = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// KT k-blocks of the channel contraction (cin = cout = W <= 16 KT), NT n-tiles of the
+// outputs (W <= 8 NT), KS k-blocks of the modes (2m <= 16 KS).  Warp w of the grid
+// takes row (b, x) = w / chunks and the y-tiles [chunk * tpw, (chunk + 1) * tpw).
+template <int KT, int NT, int KS>
+__global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, const bf16* __restrict__ Ww,
+                                                  const bf16* __restrict__ bias, const float* __restrict__ A,
+                                                  const float* __restrict__ cs, const uint4* __restrict__ TfA,
+                                                  float* __restrict__ Z, float* __restrict__ Vout, int W, int N,
+                                                  int n2m, size_t rows, int tpw, int gelu) {
+  const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
+  const int YT = (N + 15) / 16, chunks = (YT + tpw - 1) / tpw;
+  const size_t w = (size_t)blockIdx.x * 4 + threadIdx.x / 32;
+  const size_t row = w / chunks;
+  if (row >= rows) return;
+  const int chunk = (int)(w % chunks);
+  const size_t b = row / N;
+  const int x = (int)(row % N);
+  const size_t P = (size_t)N * N;
+  // B operands: W^T as stored (bf16), the row's mode coefficients split
+  unsigned wf[KT][NT][2];
+#pragma unroll
+  for (int kb = 0; kb < KT; ++kb)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int o = 8 * nt + g;
+      unsigned r2[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int c = 16 * kb + 2 * t + 8 * hh;
+        const unsigned lo = (o < W && c < W) ? (unsigned)__bfloat16_as_ushort(Ww[(size_t)o * W + c]) : 0u;
+        const unsigned hi = (o < W && c + 1 < W) ? (unsigned)__bfloat16_as_ushort(Ww[(size_t)o * W + c + 1]) : 0u;
+        r2[hh] = lo | (hi << 16);
+      }
+      wf[kb][nt][0] = r2[0];
+      wf[kb][nt][1] = r2[1];
+    }
+  unsigned sfh[KS][NT][2], sfl[KS][NT][2];
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int o = 8 * nt + g;
+      const float* ar = A + ((b * W + o) * N + x) * n2m;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int k = 16 * ks + 2 * t + 8 * hh;
+        float x0 = 0.f, x1 = 0.f;
+        if (o < W && k < n2m) x0 = ar[k] * cs[k / 2];
+        if (o < W && k + 1 < n2m) x1 = ar[k + 1] * cs[(k + 1) / 2];
+        split2(x0, x1, sfh[ks][nt][hh], sfl[ks][nt][hh]);
+      }
+    }
+  float bv[NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int o = 8 * nt + 2 * t + e;
+      bv[nt][e] = (bias != nullptr && o < W) ? b2f(bias[o]) : 0.f;
+    }
+  const float* vb = V + b * W * P + (size_t)x * N;
+  const size_t ob = b * W * P + (size_t)x * N;
+  const int yt1 = min(YT, (chunk + 1) * tpw);
+  for (int yt = chunk * tpw; yt < yt1; ++yt) {
+    const int ya = 16 * yt + g, yb = ya + 8;
+    const bool oka = ya < N, okb = yb < N;
+    unsigned ah[KT][4], al[KT][4];
+#pragma unroll
+    for (int kb = 0; kb < KT; ++kb) {
+      const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
+      auto xv = [&](int c, int y, bool ok) -> float { return (ok && c < W) ? vb[(size_t)c * P + y] : 0.f; };
+      split2(xv(c0, ya, oka), xv(c0 + 1, ya, oka), ah[kb][0], al[kb][0]);
+      split2(xv(c0, yb, okb), xv(c0 + 1, yb, okb), ah[kb][1], al[kb][1]);
+      split2(xv(c1, ya, oka), xv(c1 + 1, ya, oka), ah[kb][2], al[kb][2]);
+      split2(xv(c1, yb, okb), xv(c1 + 1, yb, okb), ah[kb][3], al[kb][3]);
+    }
+    unsigned th[KS][4], tl[KS][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const uint4* tp = TfA + (((size_t)yt * KS + ks) * 32 + lane) * 2;
+      const uint4 h4 = __ldg(tp), l4 = __ldg(tp + 1);
+      th[ks][0] = h4.x; th[ks][1] = h4.y; th[ks][2] = h4.z; th[ks][3] = h4.w;
+      tl[ks][0] = l4.x; tl[ks][1] = l4.y; tl[ks][2] = l4.z; tl[ks][3] = l4.w;
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kb = 0; kb < KT; ++kb) {
+        mma_bf16(acc, ah[kb], wf[kb][nt][0], wf[kb][nt][1]);
+        mma_bf16(acc, al[kb], wf[kb][nt][0], wf[kb][nt][1]);
+      }
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        mma_bf16(acc, th[ks], sfh[ks][nt][0], sfh[ks][nt][1]);
+        mma_bf16(acc, th[ks], sfl[ks][nt][0], sfl[ks][nt][1]);
+        mma_bf16(acc, tl[ks], sfh[ks][nt][0], sfh[ks][nt][1]);
+      }
+      // acc[0], acc[1]: pixel ya, outputs o0, o0 + 1; acc[2], acc[3]: pixel yb
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int o = 8 * nt + 2 * t + (e & 1);
+        const int y = (e < 2) ? ya : yb;
+        if (!((e < 2) ? oka : okb) || o >= W) continue;
+        const float v = acc[e] + bv[nt][e & 1];
+        const size_t at = ob + (size_t)o * P + y;
+        if (Z != nullptr) Z[at] = v;
+        Vout[at] = gelu ? gelu_f(v) : v;
+      }
+    }
+  }
+}
+
+// Fused projection (inference): out[b][p] = q2 + sum_j Q2[j] gelu(q1[j] + sum_c Q1[j][c]
+// v[b][c][p]), the hidden layer in registers: the Q1 product as in k_pw_tc, the Q2 dot
+// product in float over each lane's outputs and the four lanes of a pixel (shuffles).
+template <int KT, int NT>
+__global__ void __launch_bounds__(128) k_proj_tc(const float* __restrict__ X, int cin, const bf16* __restrict__ Q1,
+                                                 const bf16* __restrict__ q1, const bf16* __restrict__ Q2,
+                                                 const bf16* __restrict__ q2, int H, float* __restrict__ out, size_t P,
+                                                 int tpw) {
+  const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
+  const int b = blockIdx.y;
+  const size_t tiles = (P + 15) / 16;
+  const size_t tile0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * tpw;
+  if (tile0 >= tiles) return;
+  unsigned wf[KT][NT][2];
+#pragma unroll
+  for (int kb = 0; kb < KT; ++kb)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int j = 8 * nt + g;
+      unsigned r2[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int c = 16 * kb + 2 * t + 8 * hh;
+        const unsigned lo = (j < H && c < cin) ? (unsigned)__bfloat16_as_ushort(Q1[(size_t)j * cin + c]) : 0u;
+        const unsigned hi = (j < H && c + 1 < cin) ? (unsigned)__bfloat16_as_ushort(Q1[(size_t)j * cin + c + 1]) : 0u;
+        r2[hh] = lo | (hi << 16);
+      }
+      wf[kb][nt][0] = r2[0];
+      wf[kb][nt][1] = r2[1];
+    }
+  float qb[NT][2], qw[NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int j = 8 * nt + 2 * t + e;
+      qb[nt][e] = j < H ? b2f(q1[j]) : 0.f;
+      qw[nt][e] = j < H ? b2f(Q2[j]) : 0.f;
+    }
+  const float bias2 = b2f(q2[0]);
+  const float* xb = X + (size_t)b * cin * P;
+  const size_t tile1 = min(tiles, tile0 + tpw);
+  for (size_t tile = tile0; tile < tile1; ++tile) {
+    const size_t pa = tile * 16 + g, pb = pa + 8;
+    const bool oka = pa < P, okb = pb < P;
+    auto xv = [&](int c, size_t p, bool ok) -> float { return (ok && c < cin) ? xb[(size_t)c * P + p] : 0.f; };
+    unsigned ah[KT][4], al[KT][4];
+#pragma unroll
+    for (int kb = 0; kb < KT; ++kb) {
+      const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
+      split2(xv(c0, pa, oka), xv(c0 + 1, pa, oka), ah[kb][0], al[kb][0]);
+      split2(xv(c0, pb, okb), xv(c0 + 1, pb, okb), ah[kb][1], al[kb][1]);
+      split2(xv(c1, pa, oka), xv(c1 + 1, pa, oka), ah[kb][2], al[kb][2]);
+      split2(xv(c1, pb, okb), xv(c1 + 1, pb, okb), ah[kb][3], al[kb][3]);
+    }
+    float sa = 0.f, sb = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kb = 0; kb < KT; ++kb) {
+        mma_bf16(acc, ah[kb], wf[kb][nt][0], wf[kb][nt][1]);
+        mma_bf16(acc, al[kb], wf[kb][nt][0], wf[kb][nt][1]);
+      }
+      sa += qw[nt][0] * gelu_f(acc[0] + qb[nt][0]) + qw[nt][1] * gelu_f(acc[1] + qb[nt][1]);
+      sb += qw[nt][0] * gelu_f(acc[2] + qb[nt][0]) + qw[nt][1] * gelu_f(acc[3] + qb[nt][1]);
+    }
+    sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+    sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+    sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+    sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+    if (t == 0) {
+      if (oka) out[(size_t)b * P + pa] = sa + bias2;
+      if (okb) out[(size_t)b * P + pb] = sb + bias2;
+    }
+  }
+}
+
 // c_k / N^2, the weights of the gradient of the inverse transform, for the current N
 __global__ void k_cky_scaled(const float* __restrict__ c, float* __restrict__ cs, int m, float inv) {
   FOR_N(k, (size_t)m) cs[k] = c[k] * inv;
@@ -771,6 +993,7 @@ struct bem_fno_s {
   float2 *A = nullptr, *Y = nullptr, *dY = nullptr, *tw = nullptr;
   float *Tf = nullptr, *Ti = nullptr;   // twiddle matrices of the y transforms (N x 2m, 2m x N)
   uint4 *TfB = nullptr, *TiB = nullptr; // the same split into bf16 hi/lo, in mma fragment order
+  uint4* TfA = nullptr;                 // Tf split, in A-fragment order (fused layer kernel)
   double* lpart = nullptr;
   std::vector<void*> owned;
   size_t n_persistent = 0;   // leading entries of owned that live as long as the handle
@@ -787,6 +1010,13 @@ cudaError_t alloc(bem_fno_s* f, P** p, size_t count) {
 
 // the tensor-core y transforms hold up to 8 n-tiles of 2m columns (m <= 32)
 bool tc_ok(const bem_fno_s* f) { return 2 * f->d.modes <= 8 * TC_NT_MAX; }
+// the fused layer kernel: width 8, 16 or 32 (its register tiles), the same modes
+bool fused_ok(const bem_fno_s* f) {
+  const int W = f->d.width;
+  return tc_ok(f) && (W == 8 || W == 16 || W == 32);
+}
+// the fused projection: input width <= 32, hidden width <= 64
+bool proj_ok(const bem_fno_s* f) { return f->d.width <= 32 && f->d.hidden <= 64; }
 
 constexpr int kMaxSamples = 4096;
 // frees the activation buffers: everything allocated after the handle's persistent
@@ -813,6 +1043,11 @@ void set_twiddles(bem_fno_s* f, int N, cudaStream_t s) {
     k_frag_b<<<blocks_for((size_t)((N + 15) / 16) * ((n2m + 7) / 8) * 32), FT, 0, s>>>(f->Tf, N, n2m, n2m, 1, f->TfB);
     k_frag_b<<<blocks_for((size_t)((n2m + 15) / 16) * ((N + 7) / 8) * 32), FT, 0, s>>>(f->Ti, n2m, N, N, 1, f->TiB);
     note_launches(2);
+  }
+  if (fused_ok(f)) {
+    const int n2m = 2 * m;
+    k_frag_a<<<blocks_for((size_t)((N + 15) / 16) * ((n2m + 15) / 16) * 32), FT, 0, s>>>(f->Tf, N, n2m, n2m, f->TfA);
+    note_launches(1);
   }
   f->twN = N;
 }
@@ -852,6 +1087,8 @@ bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
     e = alloc(f, &f->TfB, (size_t)((N + 15) / 16) * ((2 * m + 7) / 8) * 32);
   if (e == cudaSuccess && tc_ok(f))
     e = alloc(f, &f->TiB, (size_t)((2 * m + 15) / 16) * ((N + 7) / 8) * 32);
+  if (e == cudaSuccess && fused_ok(f))
+    e = alloc(f, &f->TfA, (size_t)((N + 15) / 16) * ((2 * m + 15) / 16) * 64);
   const size_t nblk = (size_t)B * ((P + FT - 1) / FT);
   const size_t maxout = (size_t)std::max(W, H) * std::max({W, H, 7}) + std::max(W, H);
   if (e == cudaSuccess && train) e = alloc(f, &f->part, nblk * maxout);
@@ -957,7 +1194,9 @@ void idft_y(bem_fno_s* f, float* out, const float* c, float scale, size_t rows, 
                                             n2m);
 }
 
-void spectral_fwd(bem_fno_s* f, int l, const float* vin, float2* Xh, float* out, int B, int N, cudaStream_t s) {
+// spectral branch up to the inverse along x: A[(b, o, x)][2m] holds the mixed modes
+// of every row, caching dft(vin) in Xh
+void spectral_modes(bem_fno_s* f, int l, const float* vin, float2* Xh, int B, int N, cudaStream_t s) {
   const int W = f->d.width, m = f->d.modes;
   const size_t bc = (size_t)B * W, nm = 2 * (size_t)m * m;
   dft_y(f, vin, bc * N, N, s);
@@ -966,8 +1205,74 @@ void spectral_fwd(bem_fno_s* f, int l, const float* vin, float2* Xh, float* out,
   const bf16* Rim = f->wb + f->o_Rim + (size_t)l * W * W * nm;
   k_mix<<<blocks_for(bc * nm), FT, 0, s>>>(Xh, Rre, Rim, f->Y, W, (int)nm, B);
   k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
-  idft_y<false>(f, out, f->cky, 1.f / ((float)N * N), bc * N, N, s);
-  note_launches(5);
+  note_launches(4);
+}
+
+void spectral_fwd(bem_fno_s* f, int l, const float* vin, float2* Xh, float* out, int B, int N, cudaStream_t s) {
+  spectral_modes(f, l, vin, Xh, B, N, s);
+  idft_y<false>(f, out, f->cky, 1.f / ((float)N * N), (size_t)B * f->d.width * N, N, s);
+  note_launches(1);
+}
+
+template <int KT, int NT, int KS>
+void layer_launch(bem_fno_s* f, const float* vin, const bf16* Ww, const bf16* Wb, float* z, float* vout, bool gelu,
+                  int B, int N, cudaStream_t s) {
+  const int YT = (N + 15) / 16, tpw = std::min(YT, 32), chunks = (YT + tpw - 1) / tpw;
+  const size_t rows = (size_t)B * N, warps = rows * chunks;
+  k_layer_tc<KT, NT, KS><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(
+      vin, Ww, Wb, reinterpret_cast<const float*>(f->A), f->cky_s, f->TfA, z, vout, f->d.width, N, 2 * f->d.modes,
+      rows, tpw, gelu ? 1 : 0);
+}
+
+template <int KT, int NT>
+void layer_ks(bem_fno_s* f, const float* vin, const bf16* Ww, const bf16* Wb, float* z, float* vout, bool gelu, int B,
+              int N, cudaStream_t s) {
+  switch ((2 * f->d.modes + 15) / 16) {
+    case 1: layer_launch<KT, NT, 1>(f, vin, Ww, Wb, z, vout, gelu, B, N, s); break;
+    case 2: layer_launch<KT, NT, 2>(f, vin, Ww, Wb, z, vout, gelu, B, N, s); break;
+    case 3: layer_launch<KT, NT, 3>(f, vin, Ww, Wb, z, vout, gelu, B, N, s); break;
+    default: layer_launch<KT, NT, 4>(f, vin, Ww, Wb, z, vout, gelu, B, N, s); break;
+  }
+}
+
+// z = W vin + b + S(vin) (stored when z is given), vout = gelu(z) or z, in one pass
+// over the pixels after the spectral branch's mode work (fused_ok)
+void layer_fused(bem_fno_s* f, int l, const float* vin, float2* Xh, float* z, float* vout, bool gelu, int B, int N,
+                 cudaStream_t s) {
+  const int W = f->d.width;
+  spectral_modes(f, l, vin, Xh, B, N, s);
+  const bf16* Ww = f->wb + f->o_Ww + (size_t)l * W * W;
+  const bf16* Wb = f->wb + f->o_Wb + (size_t)l * W;
+  if (W == 8) layer_ks<1, 1>(f, vin, Ww, Wb, z, vout, gelu, B, N, s);
+  else if (W == 16) layer_ks<1, 2>(f, vin, Ww, Wb, z, vout, gelu, B, N, s);
+  else layer_ks<2, 4>(f, vin, Ww, Wb, z, vout, gelu, B, N, s);
+  note_launches(1);
+}
+
+template <int KT, int NT>
+void proj_launch(bem_fno_s* f, const float* v, int B, int N, cudaStream_t s) {
+  const size_t P = (size_t)N * N, tiles = (P + 15) / 16;
+  const int tpw = 8;
+  const size_t warps = (tiles + tpw - 1) / tpw;
+  k_proj_tc<KT, NT><<<dim3((unsigned)((warps + 3) / 4), B), 128, 0, s>>>(
+      v, f->d.width, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->wb + f->o_Q2w, f->wb + f->o_Q2b, f->d.hidden, f->out, P,
+      tpw);
+}
+
+template <int KT>
+void proj_nt(bem_fno_s* f, const float* v, int B, int N, cudaStream_t s) {
+  const int nt = (f->d.hidden + 7) / 8;
+  if (nt <= 1) proj_launch<KT, 1>(f, v, B, N, s);
+  else if (nt <= 2) proj_launch<KT, 2>(f, v, B, N, s);
+  else if (nt <= 4) proj_launch<KT, 4>(f, v, B, N, s);
+  else proj_launch<KT, 8>(f, v, B, N, s);
+}
+
+// out = Q2 gelu(Q1 v + q1) + q2 without storing the hidden layer (inference, proj_ok)
+void proj_fused(bem_fno_s* f, const float* v, int B, int N, cudaStream_t s) {
+  if (f->d.width <= 16) proj_nt<1>(f, v, B, N, s);
+  else proj_nt<2>(f, v, B, N, s);
+  note_launches(1);
 }
 
 bem_status forward(bem_fno_s* f, int B, int N, const float* x, bool train, cudaStream_t s) {
@@ -978,10 +1283,15 @@ bem_status forward(bem_fno_s* f, int B, int N, const float* x, bool train, cudaS
     float* vin = train ? f->v[l] : f->v[l & 1];
     float* z = train ? f->z[l] : f->z[0];
     float2* Xh = train ? f->Xh[l] : f->Xh[0];
+    float* vout = train ? f->v[l + 1] : f->v[(l + 1) & 1];
+    if (fused_ok(f)) {
+      // z is kept only for the backward pass
+      layer_fused(f, l, vin, Xh, train ? z : nullptr, vout, l < L - 1, B, N, s);
+      continue;
+    }
     spectral_fwd(f, l, vin, Xh, z, B, N, s);
     const bf16* Ww = f->wb + f->o_Ww + (size_t)l * W * W;
     const bf16* Wb = f->wb + f->o_Wb + (size_t)l * W;
-    float* vout = train ? f->v[l + 1] : f->v[(l + 1) & 1];
     if (l < L - 1) {
       pw<false, true, true>(vin, W, Ww, Wb, z, vout, W, P, B, s);
     } else {
@@ -990,8 +1300,12 @@ bem_status forward(bem_fno_s* f, int B, int N, const float* x, bool train, cudaS
     }
   }
   float* vL = train ? f->v[L] : f->v[L & 1];
-  pw<false, false, true>(vL, W, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->a, f->h, H, P, B, s);
-  pw<false, false, false>(f->h, H, f->wb + f->o_Q2w, f->wb + f->o_Q2b, f->out, nullptr, 1, P, B, s);
+  if (!train && proj_ok(f)) {
+    proj_fused(f, vL, B, N, s);
+  } else {
+    pw<false, false, true>(vL, W, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->a, f->h, H, P, B, s);
+    pw<false, false, false>(f->h, H, f->wb + f->o_Q2w, f->wb + f->o_Q2b, f->out, nullptr, 1, P, B, s);
+  }
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
