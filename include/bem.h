@@ -46,7 +46,10 @@ typedef enum {
   BEM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
   BEM_ENAN = 6,          /* non-finite value met in a reduction */
   BEM_ECYCLE = 7,        /* adhesive contact set revisited an earlier state */
-  BEM_EUNSUPPORTED = 8
+  BEM_EUNSUPPORTED = 8,  /* a valid request outside what this operator kind supports */
+  BEM_EDETACHED = 9      /* adhesive force control: the contact area vanished (the force is
+                            below what the contact can carry; under load control the
+                            indenter jumps off) */
 } bem_status;
 
 enum { BEM_FP64 = 0, BEM_FP32 = 1 };                   /* bem_kernel_desc.precision */
@@ -84,7 +87,11 @@ typedef struct bem_kernel_s* bem_kernel;
 /* One contact problem on a kernel's grid.
  *  height        indenter height map f (N*N), host or device.
  *  control       BEM_CTRL_DEPTH: target is the depth d.  BEM_CTRL_FORCE: target is
- *                the total force F = delta^2 sum p (non-adhesive only).
+ *                the total force F = delta^2 sum p and d is found: non-adhesive,
+ *                F > 0; adhesive (dgamma > 0), any finite F, starting from the
+ *                non-empty contact_mask: every fixed-area solve of the procedure
+ *                carries F (d is the multiplier of that constraint), and the
+ *                result is BEM_EDETACHED if the area vanishes on the way.
  *  dgamma        work of adhesion; 0 selects non-adhesive contact (p >= 0).  > 0
  *                runs ONE displacement-controlled step of the adhesive procedure of
  *                Sec. 2 at depth target, with the detachment stress of Eq. (12).
@@ -256,7 +263,7 @@ bem_status bem_pass_timing(bem_kernel k, double* ms_total, int64_t* launches, in
  * outputs [B][N][N].  Parameter vector order: P [width][7], p [width],
  * R_re [layers][width][width][2m][m], R_im (same), W [layers][width][width],
  * b [layers][width], Q1 [hidden][width], q1 [hidden], Q2 [hidden], q2 [1].
- * width and hidden must be one of 1, 7, 8, 16, 32, 64; N >= 2 modes. */
+ * width and hidden must be one of 1, 7, 8, 16, 32, 64; N even and N >= 2 modes. */
 typedef struct {
   int32_t width, modes, layers, hidden;
 } bem_fno_desc;
@@ -282,10 +289,11 @@ bem_status bem_fno_get_params(bem_fno f, float* params, int64_t count, int32_t r
 bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* heights, const double* params, float* x,
                             void* cuda_stream);
 /* out = network(x) for B samples (device arrays x [B][7][N][N], out [B][N][N]);
- * asynchronous on cuda_stream.  BEM_EINVAL for host arrays, B < 1 or N < 2 modes. */
+ * asynchronous on cuda_stream.  BEM_EINVAL for host arrays, B < 1, odd N or N < 2
+ * modes (the transforms read pairs of floats, 8-byte aligned for even N only). */
 bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, float* out, void* cuda_stream);
 /* forward + backward of the loss mean((out - target)^2); writes the gradient (host or
- * device, may be NULL) and the loss; synchronises the stream */
+ * device, may be NULL) and the loss; synchronises the stream.  N as for forward. */
 bem_status bem_fno_gradients(bem_fno f, int32_t B, int32_t N, const float* x, const float* target, float* grad,
                              double* loss, void* cuda_stream);
 /* one Adam step (beta 0.9/0.999, eps 1e-8) on the loss above */

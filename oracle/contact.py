@@ -24,6 +24,12 @@ p g = 0; the total force is F = delta^2 sum p.
   procedure: solve on the fixed area, add penetrating cells, detach boundary cells
   whose tension exceeds sigma_c (all at once), repeat until the area is unchanged.
 * ``adhesive_ramp``      a sequence of such steps over a list of depths.
+* ``solve_fixed_set_force``  the fixed-area problem under load control: the sum of
+  p is given and d is unknown (the multiplier of that constraint), by superposition
+  of two fixed-area solves (linearity of K).
+* ``adhesive_step_force``   the same procedure as ``adhesive_step`` with every
+  fixed-area solve carrying the given force; raises ``Detached`` when an area update
+  leaves no contact (the force is below what the contact can carry).
 
 Parity status: pinned by tests (KKT, enumeration of every contact set of a tiny
 window, NNLS, Hertz, flat punch, thin layer, JKR, Eq. 16, fixed points of the
@@ -34,6 +40,11 @@ import numpy as np
 
 class NoConvergence(RuntimeError):
     pass
+
+
+class Detached(NoConvergence):
+    """Under load control the adhesive contact area vanished: the given force is below
+    what the contact can carry (the indenter jumps off)."""
 
 
 class NotPositiveDefinite(NoConvergence):
@@ -226,3 +237,46 @@ def adhesive_ramp(matvec, f, delta, depths, sig_c, C0=None, tol=1e-13):
                         a_eq=float(np.sqrt(n * delta * delta / np.pi)), outer=outer,
                         cg_iters=its, p=p.copy(), C=C.copy()))
     return out
+
+
+def solve_fixed_set_force(matvec, C, f, P, tol=1e-13):
+    """Load control on a fixed area C: p (free in sign, 0 outside C) and d with
+    K_CC p_C = (d - f)_C and sum_C p = P (P = F / delta^2).  K is linear, so
+    p = p_f + d p_1 with K_CC p_f = -f_C and K_CC p_1 = 1_C, and the sum fixes
+    d = (P - sum p_f) / sum p_1 (sum p_1 = 1' K_CC^-1 1 > 0).  Returns (p, d, cg_iters)."""
+    pf, i1 = solve_fixed_set(matvec, C, -f, tol=tol)
+    p1, i2 = solve_fixed_set(matvec, C, np.ones_like(f), tol=tol)
+    d = (P - pf[C].sum()) / p1[C].sum()
+    return pf + d * p1, float(d), i1 + i2
+
+
+def adhesive_step_force(matvec, f, force, delta, C, sig_c, tol=1e-13, max_outer=1000):
+    """One load-controlled step of the adhesive procedure of Sec. 2: as ``adhesive_step``
+    (solve on the fixed area, add penetrating cells, detach boundary cells whose tension
+    exceeds sigma_c, repeat until the area is unchanged) with every fixed-area solve
+    carrying the total force F = delta^2 sum p, the depth following from it.  Starts
+    from the non-empty area C.  Returns (p, C, d, outer, cg_iters); raises ``Detached``
+    when an update leaves no contact."""
+    C = C.copy()
+    if not C.any():
+        raise ValueError("load control needs a non-empty starting area")
+    P = force / (delta * delta)
+    seen = set()
+    total = 0
+    for outer in range(1, max_outer + 1):
+        p, d, its = solve_fixed_set_force(matvec, C, f, P, tol=tol)
+        total += its
+        g = matvec(p) + f - d
+        add = ~C & (g < 0)
+        detach = boundary_cells(C) & (-p > sig_c)
+        if not np.any(add) and not np.any(detach):
+            return p, C, d, outer, total
+        key = (C | add) & ~detach
+        if not key.any():
+            raise Detached("the contact area vanished under the given force")
+        h = key.tobytes()
+        if h in seen:
+            raise NoConvergence("contact set cycles")
+        seen.add(h)
+        C = key
+    raise NoConvergence("adhesive outer loop did not settle")

@@ -17,9 +17,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbem.so")
 
-BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ENAN, BEM_ECYCLE, BEM_EUNSUPPORTED = range(9)
+(BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ENAN, BEM_ECYCLE, BEM_EUNSUPPORTED,
+ BEM_EDETACHED) = range(10)
 STATUS_NAMES = ["BEM_OK", "BEM_EINVAL", "BEM_ENOMEM", "BEM_ECUDA", "BEM_ENOCONV", "BEM_ETIMEOUT", "BEM_ENAN",
-                "BEM_ECYCLE", "BEM_EUNSUPPORTED"]
+                "BEM_ECYCLE", "BEM_EUNSUPPORTED", "BEM_EDETACHED"]
 BEM_FP64, BEM_FP32 = 0, 1
 BEM_CTRL_DEPTH, BEM_CTRL_FORCE = 0, 1
 BEM_DC_FINITE_PART, BEM_DC_ZERO = 0, 1
@@ -227,7 +228,7 @@ def make_problem(height, control=BEM_CTRL_DEPTH, target=0.0, dgamma=0.0, tol=1e-
                    max_iter=max_iter, target=target, dgamma=dgamma, tol=tol)
 
 
-def bem_solve_contact(k, prob, p_out, stream=None, allow=(BEM_ENOCONV,)):
+def bem_solve_contact(k, prob, p_out, stream=None, allow=(BEM_ENOCONV, BEM_EDETACHED)):
     res = Result()
     st = load().bem_solve_contact(k, ctypes.byref(prob), _ptr(p_out), ctypes.byref(res), _stream(stream))
     _check(st, allow)

@@ -93,8 +93,8 @@ bem_status check_problem(const bem_problem* prob) {
     set_error("unknown control");
     return BEM_EINVAL;
   }
-  if (prob->control == BEM_CTRL_FORCE && (prob->dgamma > 0.0 || !(prob->target > 0.0))) {
-    set_error("force control needs dgamma == 0 and a positive force");
+  if (prob->control == BEM_CTRL_FORCE && prob->dgamma == 0.0 && !(prob->target > 0.0)) {
+    set_error("non-adhesive force control needs a positive force");
     return BEM_EINVAL;
   }
   return BEM_OK;

@@ -93,6 +93,9 @@ struct SolveState {
   double tol;
   double rr, rr_new, b2;       // linear CG (adhesive inner solve)
   double alpha;
+  double qbar;       // mean of K s over the contact area (adhesive force control)
+  double lin_rbar;   // mean of the residual over the area: its rounding drift (adhesive force control)
+  double lin_shift;  // uniform pressure added on the area to carry the force (adhesive force control)
   double sig_c;      // Eq. (12) detachment stress
   uint64_t mask_hash;
   int n_c;           // contact cells at the start of the iteration

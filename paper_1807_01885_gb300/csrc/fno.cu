@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "bem_internal.cuh"
@@ -195,23 +196,38 @@ __device__ __forceinline__ int kx_of(int kxi, int m, int N) { return kxi < m ? k
 
 
 
-// A[bc][x][ky] = sum_kxi Y[bc][kxi][ky] e^{+2 pi i kx x/N}
+// A[bc][x][ky] = sum_kxi Y[bc][kxi][ky] e^{+2 pi i kx x/N}: one thread per (bc, x) and
+// four consecutive ky (one twiddle load serves four outputs)
 __global__ void k_idft_x(const float2* __restrict__ Y, float2* __restrict__ A, const float2* __restrict__ tw, int N,
                          int m, size_t bc) {
-  FOR_N(i, bc * (size_t)N * m) {
-    const size_t q = i / ((size_t)N * m);
-    const int rem = (int)(i % ((size_t)N * m));
-    const int x = rem / m, ky = rem % m;
-    const float2* y = Y + q * 2 * m * m + ky;
-    float re = 0.f, im = 0.f;
+  const int mq = (m + 3) / 4;
+  FOR_N(i, bc * (size_t)N * mq) {
+    const size_t q = i / ((size_t)N * mq);
+    const int rem = (int)(i - q * ((size_t)N * mq));
+    const int x = rem / mq, ky0 = 4 * (rem - (rem / mq) * mq);
+    const int nk = min(4, m - ky0);
+    const float2* y = Y + q * 2 * m * m + ky0;
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    // twiddle index kx x mod N, stepped by x: kx = kxi for kxi < m, kx = kxi - 2m (mod N) after
+    int idx = 0;
     for (int kxi = 0; kxi < 2 * m; ++kxi) {
-      const int kx = kx_of(kxi, m, N);
-      const float2 w = tw[(int)(((long long)kx * x) % N)];   // e^{-i theta}; conjugate below
-      const float2 v = y[(size_t)kxi * m];
-      re += v.x * w.x + v.y * w.y;
-      im += v.y * w.x - v.x * w.y;
+      if (kxi == m) idx = (int)((N - (int)(((long long)m * x) % N)) % N);
+      const float2 w = tw[idx];   // e^{-i theta}; conjugate below
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (e < nk) {
+          const float2 v = y[(size_t)kxi * m + e];
+          re[e] += v.x * w.x + v.y * w.y;
+          im[e] += v.y * w.x - v.x * w.y;
+        }
+      }
+      idx += x;
+      if (idx >= N) idx -= N;
     }
-    A[i] = make_float2(re, im);
+    float2* a = A + (q * N + x) * m + ky0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (e < nk) a[e] = make_float2(re[e], im[e]);
   }
 }
 
@@ -291,47 +307,68 @@ __global__ void k_frag_b(const float* __restrict__ Bm, int K, int Nc, size_t ldk
 
 constexpr int TC_NT_MAX = 8;   // n2m <= 64 (modes <= 32) on the tensor-core path
 
-// C[r][j] = sum_y V[r][y] Tf[y][j]: one warp per 16 rows, every n-tile of n2m
+// C[r][j] = sum_y V[r][y] Tf[y][j]: one warp per 32 rows (two m-tiles sharing every
+// B fragment), every n-tile of n2m (NT = ceil(n2m / 8))
+template <int NT>
 __global__ void __launch_bounds__(128) k_dft_y_tc(const float* __restrict__ V, const uint4* __restrict__ TfB,
                                                   float* __restrict__ C, size_t rows, int N, int n2m) {
   const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
-  const size_t R0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * 16;
+  const size_t R0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * 32;
   if (R0 >= rows) return;
-  const int KT = (N + 15) / 16, NT = (n2m + 7) / 8;
-  float acc[TC_NT_MAX][4];
+  const int KT = (N + 15) / 16;
+  float acc[2][NT][4];
 #pragma unroll
-  for (int nt = 0; nt < TC_NT_MAX; ++nt)
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
-  const size_t ra = R0 + g, rb = R0 + g + 8;
-  const float* va = V + ra * N;
-  const float* vb = V + rb * N;
-  const bool oka = ra < rows, okb = rb < rows;
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+  size_t r[2][2];
+  bool ok[2][2];
+  const float* vr[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      r[mt][h] = R0 + 16 * mt + g + 8 * h;
+      ok[mt][h] = r[mt][h] < rows;
+      vr[mt][h] = V + (ok[mt][h] ? r[mt][h] : 0) * N;
+    }
+  const bool full = (N % 16) == 0;
+#pragma unroll 2
   for (int kb = 0; kb < KT; ++kb) {
     const int k0 = 16 * kb + 2 * t, k1 = k0 + 8;
-    const float2 z = make_float2(0.f, 0.f);
-    const float2 x0 = (oka && k0 < N) ? *reinterpret_cast<const float2*>(va + k0) : z;
-    const float2 x1 = (okb && k0 < N) ? *reinterpret_cast<const float2*>(vb + k0) : z;
-    const float2 x2 = (oka && k1 < N) ? *reinterpret_cast<const float2*>(va + k1) : z;
-    const float2 x3 = (okb && k1 < N) ? *reinterpret_cast<const float2*>(vb + k1) : z;
-    unsigned ah[4], al[4];
-    split2(x0.x, x0.y, ah[0], al[0]);
-    split2(x1.x, x1.y, ah[1], al[1]);
-    split2(x2.x, x2.y, ah[2], al[2]);
-    split2(x3.x, x3.y, ah[3], al[3]);
+    unsigned ah[2][4], al[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      float2 x[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int h = e & 1, k = (e < 2) ? k0 : k1;
+        x[e] = (ok[mt][h] && (full || k < N)) ? *reinterpret_cast<const float2*>(vr[mt][h] + k)
+                                               : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split2(x[e].x, x[e].y, ah[mt][e], al[mt][e]);
+    }
     const uint4* bk = TfB + (size_t)kb * NT * 32 + lane;
 #pragma unroll
-    for (int nt = 0; nt < TC_NT_MAX; ++nt)
-      if (nt < NT) mma3(acc[nt], ah, al, bk[nt * 32]);
-  }
-#pragma unroll
-  for (int nt = 0; nt < TC_NT_MAX; ++nt) {
-    const int col = 8 * nt + 2 * t;
-    if (nt < NT && col < n2m) {
-      if (oka) *reinterpret_cast<float2*>(C + ra * n2m + col) = make_float2(acc[nt][0], acc[nt][1]);
-      if (okb) *reinterpret_cast<float2*>(C + rb * n2m + col) = make_float2(acc[nt][2], acc[nt][3]);
+    for (int nt = 0; nt < NT; ++nt) {
+      const uint4 b = bk[nt * 32];
+      mma3(acc[0][nt], ah[0], al[0], b);
+      mma3(acc[1][nt], ah[1], al[1], b);
     }
   }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int col = 8 * nt + 2 * t;
+      if (col < n2m) {
+        if (ok[mt][0]) *reinterpret_cast<float2*>(C + r[mt][0] * n2m + col) = make_float2(acc[mt][nt][0], acc[mt][nt][1]);
+        if (ok[mt][1]) *reinterpret_cast<float2*>(C + r[mt][1] * n2m + col) = make_float2(acc[mt][nt][2], acc[mt][nt][3]);
+      }
+    }
 }
 
 // out[r][y] (+)= sum_k A[r][k] cs(k) Ti[k][y], cs(k) = scale (c ? c[k/2] : 1): one
@@ -489,15 +526,17 @@ __global__ void k_frag_a(const float* __restrict__ Am, int M, int K, size_t ldr,
   }
 }
 
-// KT k-blocks of the channel contraction (cin = cout = W <= 16 KT), NT n-tiles of the
-// outputs (W <= 8 NT), KS k-blocks of the modes (2m <= 16 KS).  Warp w of the grid
-// takes row (b, x) = w / chunks and the y-tiles [chunk * tpw, (chunk + 1) * tpw).
+// NT n-tiles of the outputs (width W = 8 NT), KT = ceil(W / 16) k-blocks of the channel
+// contraction, KS k-blocks of the modes (2m <= 16 KS).  Warp w of the grid takes row
+// (b, x) = w / chunks and the y-tiles [chunk * tpw, (chunk + 1) * tpw).  Offsets
+// within one sample are 32-bit (W N^2 < 2^31).
 template <int KT, int NT, int KS>
 __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, const bf16* __restrict__ Ww,
                                                   const bf16* __restrict__ bias, const float* __restrict__ A,
                                                   const float* __restrict__ cs, const uint4* __restrict__ TfA,
-                                                  float* __restrict__ Z, float* __restrict__ Vout, int W, int N,
-                                                  int n2m, size_t rows, int tpw, int gelu) {
+                                                  float* __restrict__ Z, float* __restrict__ Vout, int N, int n2m,
+                                                  size_t rows, int tpw, int gelu) {
+  constexpr int W = 8 * NT;
   const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
   const int YT = (N + 15) / 16, chunks = (YT + tpw - 1) / tpw;
   const size_t w = (size_t)blockIdx.x * 4 + threadIdx.x / 32;
@@ -506,7 +545,7 @@ __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, c
   const int chunk = (int)(w % chunks);
   const size_t b = row / N;
   const int x = (int)(row % N);
-  const size_t P = (size_t)N * N;
+  const unsigned P = (unsigned)N * (unsigned)N;
   // B operands: W^T as stored (bf16), the row's mode coefficients split
   unsigned wf[KT][NT][2];
 #pragma unroll
@@ -514,16 +553,14 @@ __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, c
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
       const int o = 8 * nt + g;
-      unsigned r2[2];
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         const int c = 16 * kb + 2 * t + 8 * hh;
-        const unsigned lo = (o < W && c < W) ? (unsigned)__bfloat16_as_ushort(Ww[(size_t)o * W + c]) : 0u;
-        const unsigned hi = (o < W && c + 1 < W) ? (unsigned)__bfloat16_as_ushort(Ww[(size_t)o * W + c + 1]) : 0u;
-        r2[hh] = lo | (hi << 16);
+        const bool cv = 16 * kb + 8 * hh < W;   // c < W for every lane, or for none
+        const unsigned lo = cv ? (unsigned)__bfloat16_as_ushort(Ww[o * W + c]) : 0u;
+        const unsigned hi = cv ? (unsigned)__bfloat16_as_ushort(Ww[o * W + c + 1]) : 0u;
+        wf[kb][nt][hh] = lo | (hi << 16);
       }
-      wf[kb][nt][0] = r2[0];
-      wf[kb][nt][1] = r2[1];
     }
   unsigned sfh[KS][NT][2], sfl[KS][NT][2];
 #pragma unroll
@@ -535,9 +572,8 @@ __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, c
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         const int k = 16 * ks + 2 * t + 8 * hh;
-        float x0 = 0.f, x1 = 0.f;
-        if (o < W && k < n2m) x0 = ar[k] * cs[k / 2];
-        if (o < W && k + 1 < n2m) x1 = ar[k + 1] * cs[(k + 1) / 2];
+        const float x0 = k < n2m ? ar[k] * cs[k / 2] : 0.f;
+        const float x1 = k + 1 < n2m ? ar[k + 1] * cs[(k + 1) / 2] : 0.f;
         split2(x0, x1, sfh[ks][nt][hh], sfl[ks][nt][hh]);
       }
     }
@@ -545,25 +581,32 @@ __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, c
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int o = 8 * nt + 2 * t + e;
-      bv[nt][e] = (bias != nullptr && o < W) ? b2f(bias[o]) : 0.f;
-    }
-  const float* vb = V + b * W * P + (size_t)x * N;
-  const size_t ob = b * W * P + (size_t)x * N;
-  const int yt1 = min(YT, (chunk + 1) * tpw);
-  for (int yt = chunk * tpw; yt < yt1; ++yt) {
+    for (int e = 0; e < 2; ++e) bv[nt][e] = bias != nullptr ? b2f(bias[8 * nt + 2 * t + e]) : 0.f;
+  // this sample's planes, offset to row x
+  const float* vb = V + b * W * (size_t)P + (size_t)x * N;
+  const size_t ob = b * W * (size_t)P + (size_t)x * N;
+  float* zb = Z != nullptr ? Z + ob : nullptr;
+  float* ub = Vout + ob;
+  const int yt0 = chunk * tpw, yt1 = min(YT, yt0 + tpw);
+  auto tile = [&](int yt, auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
     const int ya = 16 * yt + g, yb = ya + 8;
-    const bool oka = ya < N, okb = yb < N;
+    const bool oka = FULL || ya < N, okb = FULL || yb < N;
     unsigned ah[KT][4], al[KT][4];
 #pragma unroll
     for (int kb = 0; kb < KT; ++kb) {
-      const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
-      auto xv = [&](int c, int y, bool ok) -> float { return (ok && c < W) ? vb[(size_t)c * P + y] : 0.f; };
-      split2(xv(c0, ya, oka), xv(c0 + 1, ya, oka), ah[kb][0], al[kb][0]);
-      split2(xv(c0, yb, okb), xv(c0 + 1, yb, okb), ah[kb][1], al[kb][1]);
-      split2(xv(c1, ya, oka), xv(c1 + 1, ya, oka), ah[kb][2], al[kb][2]);
-      split2(xv(c1, yb, okb), xv(c1 + 1, yb, okb), ah[kb][3], al[kb][3]);
+      float xv[4][2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const bool cv = 16 * kb + 8 * hh < W;
+          const float* pc = vb + (unsigned)(16 * kb + 2 * t + 8 * hh + e) * P;
+          xv[2 * hh][e] = (cv && oka) ? pc[ya] : 0.f;
+          xv[2 * hh + 1][e] = (cv && okb) ? pc[yb] : 0.f;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) split2(xv[r][0], xv[r][1], ah[kb][r], al[kb][r]);
     }
     unsigned th[KS][4], tl[KS][4];
 #pragma unroll
@@ -589,30 +632,184 @@ __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, c
       }
       // acc[0], acc[1]: pixel ya, outputs o0, o0 + 1; acc[2], acc[3]: pixel yb
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int o = 8 * nt + 2 * t + (e & 1);
-        const int y = (e < 2) ? ya : yb;
-        if (!((e < 2) ? oka : okb) || o >= W) continue;
-        const float v = acc[e] + bv[nt][e & 1];
-        const size_t at = ob + (size_t)o * P + y;
-        if (Z != nullptr) Z[at] = v;
-        Vout[at] = gelu ? gelu_f(v) : v;
+      for (int e = 0; e < 2; ++e) {
+        const unsigned oo = (unsigned)(8 * nt + 2 * t + e) * P;
+        const float va = acc[e] + bv[nt][e], vb2 = acc[2 + e] + bv[nt][e];
+        if (zb != nullptr) {
+          if (oka) zb[oo + ya] = va;
+          if (okb) zb[oo + yb] = vb2;
+        }
+        if (oka) ub[oo + ya] = gelu ? gelu_f(va) : va;
+        if (okb) ub[oo + yb] = gelu ? gelu_f(vb2) : vb2;
       }
     }
+  };
+  if (N % 16 == 0) {
+    for (int yt = yt0; yt < yt1; ++yt) tile(yt, std::true_type{});
+  } else {
+    for (int yt = yt0; yt < yt1; ++yt) tile(yt, std::false_type{});
   }
+}
+
+// 16-byte asynchronous global -> shared copies (L2 only), committed in groups
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// The fused layer for N a multiple of 16, with the activations of the next y-tile
+// copied to shared memory (cp.async, two stages per warp) while the current one is
+// contracted: each warp stages its W channels x 16 pixels (W 64-byte rows, row stride
+// 20 floats, which makes the fragment reads conflict-free).  Same arithmetic and
+// order as k_layer_tc.
+constexpr int kLayerRow = 20;
+template <int KT, int NT, int KS>
+__global__ void __launch_bounds__(128, 4) k_layer_tc_pipe(const float* __restrict__ V, const bf16* __restrict__ Ww,
+                                                       const bf16* __restrict__ bias, const float* __restrict__ A,
+                                                       const float* __restrict__ cs, const uint4* __restrict__ TfA,
+                                                       float* __restrict__ Z, float* __restrict__ Vout, int N, int n2m,
+                                                       size_t rows, int tpw, int gelu) {
+  constexpr int W = 8 * NT, STAGE = W * kLayerRow;
+  __shared__ __align__(16) float sbuf[4][2][STAGE];
+  const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4, wid = threadIdx.x / 32;
+  const int YT = N / 16, chunks = (YT + tpw - 1) / tpw;
+  const size_t w = (size_t)blockIdx.x * 4 + wid;
+  const size_t row = w / chunks;
+  if (row >= rows) return;
+  const int chunk = (int)(w % chunks);
+  const size_t b = row / N;
+  const int x = (int)(row % N);
+  const unsigned P = (unsigned)N * (unsigned)N;
+  unsigned wf[KT][NT][2];
+#pragma unroll
+  for (int kb = 0; kb < KT; ++kb)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int o = 8 * nt + g;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int c = 16 * kb + 2 * t + 8 * hh;
+        const bool cv = 16 * kb + 8 * hh < W;
+        const unsigned lo = cv ? (unsigned)__bfloat16_as_ushort(Ww[o * W + c]) : 0u;
+        const unsigned hi = cv ? (unsigned)__bfloat16_as_ushort(Ww[o * W + c + 1]) : 0u;
+        wf[kb][nt][hh] = lo | (hi << 16);
+      }
+    }
+  unsigned sfh[KS][NT][2], sfl[KS][NT][2];
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int o = 8 * nt + g;
+      const float* ar = A + ((b * W + o) * N + x) * n2m;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int k = 16 * ks + 2 * t + 8 * hh;
+        const float x0 = k < n2m ? ar[k] * cs[k / 2] : 0.f;
+        const float x1 = k + 1 < n2m ? ar[k + 1] * cs[(k + 1) / 2] : 0.f;
+        split2(x0, x1, sfh[ks][nt][hh], sfl[ks][nt][hh]);
+      }
+    }
+  float bv[NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) bv[nt][e] = bias != nullptr ? b2f(bias[8 * nt + 2 * t + e]) : 0.f;
+  const float* vb = V + b * W * (size_t)P + (size_t)x * N;
+  const size_t ob = b * W * (size_t)P + (size_t)x * N;
+  float* zb = Z != nullptr ? Z + ob : nullptr;
+  float* ub = Vout + ob;
+  float(*buf)[STAGE] = sbuf[wid];
+  // tile yt -> stage st: W rows of 16 floats, four 16-byte pieces each
+  auto prefetch = [&](int yt, int st) {
+#pragma unroll
+    for (int j = lane; j < 4 * W; j += 32) {
+      const int c = j >> 2, part = j & 3;
+      cp_async16(&buf[st][c * kLayerRow + 4 * part], vb + (unsigned)c * P + 16 * yt + 4 * part);
+    }
+    cp_async_commit();
+  };
+  const int yt0 = chunk * tpw, yt1 = min(YT, yt0 + tpw);
+  if (yt0 < yt1) prefetch(yt0, 0);
+  int st = 0;
+  for (int yt = yt0; yt < yt1; ++yt) {
+    if (yt + 1 < yt1) prefetch(yt + 1, st ^ 1);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    const float* sb = buf[st];
+    const int ya = 16 * yt + g, yb = ya + 8;
+    unsigned ah[KT][4], al[KT][4];
+#pragma unroll
+    for (int kb = 0; kb < KT; ++kb) {
+      float xv[4][2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const bool cv = 16 * kb + 8 * hh < W;
+          const int c = 16 * kb + 2 * t + 8 * hh + e;
+          xv[2 * hh][e] = cv ? sb[c * kLayerRow + g] : 0.f;
+          xv[2 * hh + 1][e] = cv ? sb[c * kLayerRow + g + 8] : 0.f;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) split2(xv[r][0], xv[r][1], ah[kb][r], al[kb][r]);
+    }
+    __syncwarp();   // every lane has read the stage before it is refilled
+    unsigned th[KS][4], tl[KS][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const uint4* tp = TfA + (((size_t)yt * KS + ks) * 32 + lane) * 2;
+      const uint4 h4 = __ldg(tp), l4 = __ldg(tp + 1);
+      th[ks][0] = h4.x; th[ks][1] = h4.y; th[ks][2] = h4.z; th[ks][3] = h4.w;
+      tl[ks][0] = l4.x; tl[ks][1] = l4.y; tl[ks][2] = l4.z; tl[ks][3] = l4.w;
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kb = 0; kb < KT; ++kb) {
+        mma_bf16(acc, ah[kb], wf[kb][nt][0], wf[kb][nt][1]);
+        mma_bf16(acc, al[kb], wf[kb][nt][0], wf[kb][nt][1]);
+      }
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        mma_bf16(acc, th[ks], sfh[ks][nt][0], sfh[ks][nt][1]);
+        mma_bf16(acc, th[ks], sfl[ks][nt][0], sfl[ks][nt][1]);
+        mma_bf16(acc, tl[ks], sfh[ks][nt][0], sfh[ks][nt][1]);
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const unsigned oo = (unsigned)(8 * nt + 2 * t + e) * P;
+        const float va = acc[e] + bv[nt][e], vb2 = acc[2 + e] + bv[nt][e];
+        if (zb != nullptr) {
+          zb[oo + ya] = va;
+          zb[oo + yb] = vb2;
+        }
+        ub[oo + ya] = gelu ? gelu_f(va) : va;
+        ub[oo + yb] = gelu ? gelu_f(vb2) : vb2;
+      }
+    }
+    st ^= 1;
+  }
+  cp_async_wait<0>();
 }
 
 // Fused projection (inference): out[b][p] = q2 + sum_j Q2[j] gelu(q1[j] + sum_c Q1[j][c]
 // v[b][c][p]), the hidden layer in registers: the Q1 product as in k_pw_tc, the Q2 dot
 // product in float over each lane's outputs and the four lanes of a pixel (shuffles).
+// Offsets within one sample are 32-bit (cin N^2 < 2^32).
 template <int KT, int NT>
 __global__ void __launch_bounds__(128) k_proj_tc(const float* __restrict__ X, int cin, const bf16* __restrict__ Q1,
                                                  const bf16* __restrict__ q1, const bf16* __restrict__ Q2,
-                                                 const bf16* __restrict__ q2, int H, float* __restrict__ out, size_t P,
+                                                 const bf16* __restrict__ q2, int H, float* __restrict__ out, unsigned P,
                                                  int tpw) {
   const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
   const int b = blockIdx.y;
-  const size_t tiles = (P + 15) / 16;
+  const unsigned tiles = (P + 15) / 16;
   const size_t tile0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * tpw;
   if (tile0 >= tiles) return;
   unsigned wf[KT][NT][2];
@@ -621,16 +818,13 @@ __global__ void __launch_bounds__(128) k_proj_tc(const float* __restrict__ X, in
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
       const int j = 8 * nt + g;
-      unsigned r2[2];
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         const int c = 16 * kb + 2 * t + 8 * hh;
-        const unsigned lo = (j < H && c < cin) ? (unsigned)__bfloat16_as_ushort(Q1[(size_t)j * cin + c]) : 0u;
-        const unsigned hi = (j < H && c + 1 < cin) ? (unsigned)__bfloat16_as_ushort(Q1[(size_t)j * cin + c + 1]) : 0u;
-        r2[hh] = lo | (hi << 16);
+        const unsigned lo = (j < H && c < cin) ? (unsigned)__bfloat16_as_ushort(Q1[j * cin + c]) : 0u;
+        const unsigned hi = (j < H && c + 1 < cin) ? (unsigned)__bfloat16_as_ushort(Q1[j * cin + c + 1]) : 0u;
+        wf[kb][nt][hh] = lo | (hi << 16);
       }
-      wf[kb][nt][0] = r2[0];
-      wf[kb][nt][1] = r2[1];
     }
   float qb[NT][2], qw[NT][2];
 #pragma unroll
@@ -643,19 +837,27 @@ __global__ void __launch_bounds__(128) k_proj_tc(const float* __restrict__ X, in
     }
   const float bias2 = b2f(q2[0]);
   const float* xb = X + (size_t)b * cin * P;
-  const size_t tile1 = min(tiles, tile0 + tpw);
-  for (size_t tile = tile0; tile < tile1; ++tile) {
-    const size_t pa = tile * 16 + g, pb = pa + 8;
-    const bool oka = pa < P, okb = pb < P;
-    auto xv = [&](int c, size_t p, bool ok) -> float { return (ok && c < cin) ? xb[(size_t)c * P + p] : 0.f; };
+  float* ob = out + (size_t)b * P;
+  const unsigned t1 = (unsigned)min((size_t)tiles, tile0 + tpw);
+  auto tile = [&](unsigned tl, auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    const unsigned pa = tl * 16 + g, pb = pa + 8;
+    const bool oka = FULL || pa < P, okb = FULL || pb < P;
     unsigned ah[KT][4], al[KT][4];
 #pragma unroll
     for (int kb = 0; kb < KT; ++kb) {
-      const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
-      split2(xv(c0, pa, oka), xv(c0 + 1, pa, oka), ah[kb][0], al[kb][0]);
-      split2(xv(c0, pb, okb), xv(c0 + 1, pb, okb), ah[kb][1], al[kb][1]);
-      split2(xv(c1, pa, oka), xv(c1 + 1, pa, oka), ah[kb][2], al[kb][2]);
-      split2(xv(c1, pb, okb), xv(c1 + 1, pb, okb), ah[kb][3], al[kb][3]);
+      float xv[4][2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = 16 * kb + 2 * t + 8 * hh + e;
+          const float* pc = xb + (unsigned)c * P;
+          xv[2 * hh][e] = (c < cin && oka) ? pc[pa] : 0.f;
+          xv[2 * hh + 1][e] = (c < cin && okb) ? pc[pb] : 0.f;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) split2(xv[r][0], xv[r][1], ah[kb][r], al[kb][r]);
     }
     float sa = 0.f, sb = 0.f;
 #pragma unroll
@@ -674,9 +876,14 @@ __global__ void __launch_bounds__(128) k_proj_tc(const float* __restrict__ X, in
     sb += __shfl_xor_sync(0xffffffffu, sb, 1);
     sb += __shfl_xor_sync(0xffffffffu, sb, 2);
     if (t == 0) {
-      if (oka) out[(size_t)b * P + pa] = sa + bias2;
-      if (okb) out[(size_t)b * P + pb] = sb + bias2;
+      if (oka) ob[pa] = sa + bias2;
+      if (okb) ob[pb] = sb + bias2;
     }
+  };
+  if (P % 16 == 0) {
+    for (unsigned tl = (unsigned)tile0; tl < t1; ++tl) tile(tl, std::true_type{});
+  } else {
+    for (unsigned tl = (unsigned)tile0; tl < t1; ++tl) tile(tl, std::false_type{});
   }
 }
 
@@ -823,11 +1030,16 @@ __global__ void __launch_bounds__(256) k_dft_x_par(const float2* __restrict__ A,
   float re = 0.f, im = 0.f;
   if (slice < S) {
     const float2* a = A + q * (size_t)N * m + ky;
+    // twiddle index kx x mod N, stepped by kx S mod N
+    int idx = (int)(((long long)kx * slice) % N);
+    const int step = (int)(((long long)kx * S) % N);
     for (int x = slice; x < N; x += S) {
-      const float2 w = tw[((size_t)kx * x) % N];
+      const float2 w = tw[idx];
       const float2 v = a[(size_t)x * m];
       re += v.x * w.x - v.y * w.y;
       im += v.x * w.y + v.y * w.x;
+      idx += step;
+      if (idx >= N) idx -= N;
     }
   }
   red[threadIdx.x] = make_float2(re, im);
@@ -1173,7 +1385,18 @@ void wgrad(const float* dY, int cout, const float* X, int cin, float* gw, float*
 void dft_y(bem_fno_s* f, const float* v, size_t rows, int N, cudaStream_t s) {
   const int n2m = 2 * f->d.modes;
   if (tc_ok(f)) {
-    k_dft_y_tc<<<(unsigned)((rows + 63) / 64), 128, 0, s>>>(v, f->TfB, reinterpret_cast<float*>(f->A), rows, N, n2m);
+    const unsigned grid = (unsigned)((rows + 127) / 128);
+    float* C = reinterpret_cast<float*>(f->A);
+    switch ((n2m + 7) / 8) {
+      case 1: k_dft_y_tc<1><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      case 2: k_dft_y_tc<2><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      case 3: k_dft_y_tc<3><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      case 4: k_dft_y_tc<4><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      case 5: k_dft_y_tc<5><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      case 6: k_dft_y_tc<6><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      case 7: k_dft_y_tc<7><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+      default: k_dft_y_tc<8><<<grid, 128, 0, s>>>(v, f->TfB, C, rows, N, n2m); break;
+    }
     return;
   }
   const dim3 grid((unsigned)((rows + G1_BM - 1) / G1_BM), (unsigned)((n2m + G1_BN - 1) / G1_BN));
@@ -1204,7 +1427,7 @@ void spectral_modes(bem_fno_s* f, int l, const float* vin, float2* Xh, int B, in
   const bf16* Rre = f->wb + f->o_Rre + (size_t)l * W * W * nm;
   const bf16* Rim = f->wb + f->o_Rim + (size_t)l * W * W * nm;
   k_mix<<<blocks_for(bc * nm), FT, 0, s>>>(Xh, Rre, Rim, f->Y, W, (int)nm, B);
-  k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
+  k_idft_x<<<blocks_for(bc * N * ((m + 3) / 4)), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
   note_launches(4);
 }
 
@@ -1219,9 +1442,15 @@ void layer_launch(bem_fno_s* f, const float* vin, const bf16* Ww, const bf16* Wb
                   int B, int N, cudaStream_t s) {
   const int YT = (N + 15) / 16, tpw = std::min(YT, 32), chunks = (YT + tpw - 1) / tpw;
   const size_t rows = (size_t)B * N, warps = rows * chunks;
+  if (N % 16 == 0) {   // whole 16-pixel tiles, 16-byte aligned rows: the staged form
+    k_layer_tc_pipe<KT, NT, KS><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(
+        vin, Ww, Wb, reinterpret_cast<const float*>(f->A), f->cky_s, f->TfA, z, vout, N, 2 * f->d.modes, rows, tpw,
+        gelu ? 1 : 0);
+    return;
+  }
   k_layer_tc<KT, NT, KS><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(
-      vin, Ww, Wb, reinterpret_cast<const float*>(f->A), f->cky_s, f->TfA, z, vout, f->d.width, N, 2 * f->d.modes,
-      rows, tpw, gelu ? 1 : 0);
+      vin, Ww, Wb, reinterpret_cast<const float*>(f->A), f->cky_s, f->TfA, z, vout, N, 2 * f->d.modes, rows, tpw,
+      gelu ? 1 : 0);
 }
 
 template <int KT, int NT>
@@ -1255,8 +1484,8 @@ void proj_launch(bem_fno_s* f, const float* v, int B, int N, cudaStream_t s) {
   const int tpw = 8;
   const size_t warps = (tiles + tpw - 1) / tpw;
   k_proj_tc<KT, NT><<<dim3((unsigned)((warps + 3) / 4), B), 128, 0, s>>>(
-      v, f->d.width, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->wb + f->o_Q2w, f->wb + f->o_Q2b, f->d.hidden, f->out, P,
-      tpw);
+      v, f->d.width, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->wb + f->o_Q2w, f->wb + f->o_Q2b, f->d.hidden, f->out,
+      (unsigned)P, tpw);
 }
 
 template <int KT>
@@ -1284,7 +1513,7 @@ bem_status forward(bem_fno_s* f, int B, int N, const float* x, bool train, cudaS
     float* z = train ? f->z[l] : f->z[0];
     float2* Xh = train ? f->Xh[l] : f->Xh[0];
     float* vout = train ? f->v[l + 1] : f->v[(l + 1) & 1];
-    if (fused_ok(f)) {
+    if (fused_ok(f) && (size_t)W * P < (size_t(1) << 32)) {   // 32-bit offsets within a sample
       // z is kept only for the backward pass
       layer_fused(f, l, vin, Xh, train ? z : nullptr, vout, l < L - 1, B, N, s);
       continue;
@@ -1300,7 +1529,7 @@ bem_status forward(bem_fno_s* f, int B, int N, const float* x, bool train, cudaS
     }
   }
   float* vL = train ? f->v[L] : f->v[L & 1];
-  if (!train && proj_ok(f)) {
+  if (!train && proj_ok(f) && (size_t)W * P < (size_t(1) << 32)) {
     proj_fused(f, vL, B, N, s);
   } else {
     pw<false, false, true>(vL, W, f->wb + f->o_Q1w, f->wb + f->o_Q1b, f->a, f->h, H, P, B, s);
@@ -1344,7 +1573,7 @@ bem_status backward(bem_fno_s* f, int B, int N, const float* x, const float* tar
                                                           f->g + f->o_Rim + (size_t)l * W * W * nm, W, (int)nm, B);
     k_mix_dgrad<<<blocks_for(bc * nm), FT, 0, s>>>(f->dY, Rre, Rim, f->Y, W, (int)nm, B);
     // d_vin += Re(sum dXh e^{+i theta}) (adjoint of the forward transform)
-    k_idft_x<<<blocks_for(bc * N * m), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
+    k_idft_x<<<blocks_for(bc * N * ((m + 3) / 4)), FT, 0, s>>>(f->Y, f->A, f->tw, N, m, bc);
     idft_y<true>(f, f->dt, nullptr, 1.f, bc * N, N, s);
     note_launches(6);
     std::swap(f->dv, f->dt);
@@ -1480,8 +1709,8 @@ bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* height
 }
 
 bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, float* out, void* cuda_stream) {
-  if (f == nullptr || x == nullptr || out == nullptr || B < 1 || N < 2 * f->d.modes) {
-    set_error("invalid FNO forward arguments (N must be at least twice the retained modes)");
+  if (f == nullptr || x == nullptr || out == nullptr || B < 1 || N < 2 * f->d.modes || N % 2 != 0) {
+    set_error("invalid FNO forward arguments (N must be even and at least twice the retained modes)");
     return BEM_EINVAL;
   }
   if (!is_dev(x) || !is_dev(out)) { set_error("FNO arrays must be device arrays"); return BEM_EINVAL; }
@@ -1496,8 +1725,9 @@ bem_status bem_fno_forward(bem_fno f, int32_t B, int32_t N, const float* x, floa
 
 bem_status bem_fno_gradients(bem_fno f, int32_t B, int32_t N, const float* x, const float* target, float* grad,
                              double* loss, void* cuda_stream) {
-  if (f == nullptr || x == nullptr || target == nullptr || loss == nullptr || B < 1 || N < 2 * f->d.modes) {
-    set_error("invalid FNO gradient arguments");
+  if (f == nullptr || x == nullptr || target == nullptr || loss == nullptr || B < 1 || N < 2 * f->d.modes ||
+      N % 2 != 0) {
+    set_error("invalid FNO gradient arguments (N must be even and at least twice the retained modes)");
     return BEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;

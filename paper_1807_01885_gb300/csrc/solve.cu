@@ -484,6 +484,7 @@ template <typename T>
 __global__ void k_lin_init(const T* __restrict__ u, const T* __restrict__ f, const uint8_t* __restrict__ C,
                            T* __restrict__ r, T* __restrict__ s, double* partials, unsigned int* ticket,
                            SolveState* st, size_t n) {
+  if (st->status != BEM_OK) return;   // the force-control set-up found no contact area
   const double d = st->d;
   const T dT = (T)d;
   Acc<T> arr, abb;
@@ -510,21 +511,34 @@ __global__ void k_lin_init(const T* __restrict__ u, const T* __restrict__ f, con
   }
 }
 
+// alpha = <r, r> / <s, K s> on C; under force control also the means of K s and of r
+// over C (r is zero-mean in exact arithmetic; its mean is the rounding drift that the
+// update removes, so that the residual can fall below the drift's level)
 template <typename T>
-__global__ void k_lin_alpha(const T* __restrict__ s, const T* __restrict__ q, const uint8_t* __restrict__ C,
-                            double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+__global__ void k_lin_alpha(const T* __restrict__ s, const T* __restrict__ q, const T* __restrict__ r,
+                            const uint8_t* __restrict__ C, double* partials, unsigned int* ticket, SolveState* st,
+                            size_t n) {
   if (st->done) return;
-  Acc<T> a;
-  GRID_STRIDE(i, n) if (C[i]) a.add(s[i] * q[i]);
-  Acc<T> v[1] = {a};
-  double tot[1];
-  if (grid_reduce<1>(v, partials, ticket, tot)) {
+  const bool force = st->control == BEM_CTRL_FORCE;
+  Acc<T> a, aq, ar;
+  GRID_STRIDE(i, n) if (C[i]) {
+    a.add(s[i] * q[i]);
+    if (force) {
+      aq.add(q[i]);
+      ar.add(r[i]);
+    }
+  }
+  Acc<T> v[3] = {a, aq, ar};
+  double tot[3];
+  if (grid_reduce<3>(v, partials, ticket, tot)) {
     const double alpha = st->rr / tot[0];
     if (!(tot[0] > 0.0) || !isfinite(alpha)) {
       finish(st, BEM_ENAN);
       return;
     }
     st->alpha = alpha;
+    st->qbar = force ? (double)(T)(tot[1] / (double)st->n_c) : 0.0;
+    st->lin_rbar = force ? (double)(T)(tot[2] / (double)st->n_c) : 0.0;
   }
 }
 
@@ -534,11 +548,12 @@ __global__ void k_lin_update(T* __restrict__ x, T* __restrict__ r, const T* __re
                              size_t n) {
   if (st->done) return;
   const T alpha = (T)st->alpha;
+  const T qbar = (T)st->qbar, rbar = (T)st->lin_rbar;   // 0 under depth control
   Acc<T> arr;
   GRID_STRIDE(i, n) {
     if (C[i]) {
       x[i] += alpha * s[i];
-      const T ri = r[i] - alpha * q[i];
+      const T ri = (r[i] - rbar) - alpha * (q[i] - qbar);
       r[i] = ri;
       arr.add(ri * ri);
     }
@@ -546,6 +561,9 @@ __global__ void k_lin_update(T* __restrict__ x, T* __restrict__ r, const T* __re
   Acc<T> v[1] = {arr};
   double tot[1];
   if (grid_reduce<1>(v, partials, ticket, tot)) {
+    // force control: the depth moves with the mean of the step's displacement, which
+    // keeps the residual d - f - K x at zero mean over C
+    if (st->control == BEM_CTRL_FORCE) st->d += st->alpha * st->qbar - st->lin_rbar;
     st->beta = tot[0] / st->rr;
     st->rr = tot[0];
     st->iter += 1;
@@ -567,6 +585,49 @@ __global__ void k_lin_dir(const T* __restrict__ r, T* __restrict__ s, const uint
   if (st->done) return;
   const T beta = (T)st->beta;
   GRID_STRIDE(i, n) s[i] = C[i] ? r[i] + beta * s[i] : (T)0;
+}
+
+// Adhesive force control (Sec. 2 procedure at a given total force F): the fixed-area
+// CG runs on the pressures with delta^2 sum_C x = F, the depth d being the multiplier
+// of that constraint.  Before each fixed-area solve, x is shifted uniformly on C to
+// carry F (x loses pressure outside the area at every area update); after the first
+// product, d = mean_C (f + K x), which makes the residual d - f - K x zero-mean on C.
+template <typename T>
+__global__ void k_lin_force_sum(const T* __restrict__ x, const uint8_t* __restrict__ C, double* partials,
+                                unsigned int* ticket, SolveState* st, size_t n) {
+  Acc<T> ax, ac;
+  GRID_STRIDE(i, n) if (C[i]) {
+    ax.add(x[i]);
+    ac.add((T)1);
+  }
+  Acc<T> v[2] = {ax, ac};
+  double tot[2];
+  if (grid_reduce<2>(v, partials, ticket, tot)) {
+    st->n_c = (int)tot[1];
+    if (st->n_c == 0) {
+      finish(st, BEM_EDETACHED);
+      return;
+    }
+    st->lin_shift = (st->target / st->delta2 - tot[0]) / tot[1];
+  }
+}
+
+template <typename T>
+__global__ void k_lin_force_shift(T* __restrict__ x, const uint8_t* __restrict__ C, const SolveState* st, size_t n) {
+  if (st->done) return;
+  const T sh = (T)st->lin_shift;
+  GRID_STRIDE(i, n) if (C[i]) x[i] += sh;
+}
+
+template <typename T>
+__global__ void k_lin_force_depth(const T* __restrict__ u, const T* __restrict__ f, const uint8_t* __restrict__ C,
+                                  double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  if (st->done) return;
+  Acc<T> a;
+  GRID_STRIDE(i, n) if (C[i]) a.add(f[i] + u[i]);
+  Acc<T> v[1] = {a};
+  double tot[1];
+  if (grid_reduce<1>(v, partials, ticket, tot)) st->d = (double)(T)(tot[0] / (double)st->n_c);
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -975,7 +1036,7 @@ void lin_chunk_launches(bem_kernel_s* k, const uint8_t* C, cudaStream_t s) {
   unsigned int* tk = k->ws.ticket;
   for (int it = 0; it < CHUNK; ++it) {
     launch_matvec<T>(k, v.t, v.g, s, &st->mv_t_on);
-    k_lin_alpha<T><<<c.rb, NTHREADS, 0, s>>>(v.t, v.g, C, part, tk, st, c.n);
+    k_lin_alpha<T><<<c.rb, NTHREADS, 0, s>>>(v.t, v.g, v.r, C, part, tk, st, c.n);
     k_lin_update<T><<<c.rb, NTHREADS, 0, s>>>(v.x, v.r, v.t, v.g, C, part, tk, st, c.n);
     k_lin_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.r, v.t, C, st, c.n);
     note_launches(3);
@@ -1024,7 +1085,9 @@ bem_status run_pk(bem_kernel_s* k, const bem_problem* prob, const T* pinit, cuda
 
 template <typename T>
 bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit, uint8_t* mask_dev,
-                        int* outer_out, int* iters_out, int* mv_out, double* res_out, cudaStream_t s) {
+                        int* outer_out, int* iters_out, int* mv_out, double* res_out, double* d_out, cudaStream_t s) {
+  const bool force = prob->control == BEM_CTRL_FORCE;
+  *d_out = prob->target;
   const Ctx c = ctx_of<T>(k);
   DV<T> v = dv<T>(k);
   SolveState* st = k->ws.state;
@@ -1053,7 +1116,9 @@ bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit
   const int max_outer = 1000;
   for (outer = 1; outer <= max_outer; ++outer) {
     SolveState init{};
-    init.d = prob->target;
+    init.d = force ? *d_out : prob->target;
+    init.target = prob->target;
+    init.control = prob->control;
     init.tol = prob->tol;
     init.max_iter = prob->max_iter;
     init.sig_c = sig_c;
@@ -1062,8 +1127,17 @@ bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit
     init.mv_t_on = 1;
     *hs = init;
     BEM_CUDA_TRY(cudaMemcpyAsync(st, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    if (force) {   // x carries F on C
+      k_lin_force_sum<T><<<c.rb, NTHREADS, 0, s>>>(v.x, C, part, tk, st, c.n);
+      k_lin_force_shift<T><<<c.eb, NTHREADS, 0, s>>>(v.x, C, st, c.n);
+      note_launches(2);
+    }
     // CG on K_CC x = (d - f)_C
     launch_matvec<T>(k, v.x, v.u, s, nullptr);
+    if (force) {
+      k_lin_force_depth<T><<<c.rb, NTHREADS, 0, s>>>(v.u, v.f, C, part, tk, st, c.n);
+      note_launches(1);
+    }
     k_lin_init<T><<<c.rb, NTHREADS, 0, s>>>(v.u, v.f, C, v.r, v.t, part, tk, st, c.n);
     note_launches(1);
     mv += 1;
@@ -1077,8 +1151,16 @@ bem_status run_adhesive(bem_kernel_s* k, const bem_problem* prob, const T* pinit
     iters += hs->iter;
     mv += hs->matvecs;
     res = hs->res;
+    if (force) *d_out = hs->d;
     if (hs->status != BEM_OK) {
       *outer_out = outer; *iters_out = iters; *mv_out = mv; *res_out = res;
+      if (hs->status == BEM_EDETACHED) {
+        if (outer == 1) {   // the given starting area was empty
+          set_error("force-controlled adhesive solve needs a non-empty starting contact area");
+          return BEM_EINVAL;
+        }
+        set_error("the contact area vanished under the given force");
+      }
       return (bem_status)hs->status;
     }
     // area update from the fresh gap
@@ -1157,7 +1239,7 @@ bem_status solve_typed(bem_kernel_s* k, const bem_problem* prob, const T* f, con
   if (prob->dgamma > 0.0) {
     int outer = 0, iters = 0, mv = 0;
     double r = 0.0;
-    st = run_adhesive<T>(k, prob, pinit, mask, &outer, &iters, &mv, &r, s);
+    st = run_adhesive<T>(k, prob, pinit, mask, &outer, &iters, &mv, &r, &d, s);
     res->outer_iters = outer;
     res->iters = iters;
     res->matvecs = mv;

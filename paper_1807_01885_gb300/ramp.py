@@ -1,7 +1,8 @@
 """Displacement-controlled adhesive ramps (loading, then pull-off), as in Sec. 2.
 
 Orchestration only: each step is one bem_solve_contact call with dgamma > 0 at the
-step's depth; the pressure and the contact mask carry over from step to step.  The
+step's depth (``run``) or force (``force_steps``, the force control inside the
+library); the pressure and the contact mask carry over from step to step.  The
 ramp state can be saved every few steps and a saved ramp resumed: the resumed steps
 repeat the same trajectory (same inputs, same device-side arithmetic).
 """
@@ -22,7 +23,7 @@ def run(kernel, height, depths, dgamma, tol=1e-8, max_iter=20000, state=None, ch
     on ``stream`` (default: a stream of the ramp's own, on which the library replays
     its captured iteration graphs; every solve synchronises its stream).
     ``with_state``: return (records, (p, mask)) with the device state after the last
-    step, e.g. to continue under force control (``force_run``)."""
+    step, e.g. to continue under force control (``force_steps``)."""
     if stream is None:
         stream = torch.cuda.Stream(device=height.device)
     with torch.cuda.stream(stream):
@@ -59,99 +60,28 @@ def load_state(path):
     return int(z["step"]), z["p"], z["mask"]
 
 
-def force_pull_off(solve_depth, forces, d0, state0, F0, stiffness, rtol=2e-3, max_step=np.inf, max_trials=400,
-                   max_halvings=14):
-    """Force-controlled pull-off over decreasing force targets, as a search over the
-    depth-controlled steps of the Sec. 2 procedure.
-
-    ``solve_depth(d, state) -> (state', F, n_contact)`` runs one displacement-controlled
-    adhesive step at depth d starting from ``state`` (which it must not modify).  The
-    procedure depends on the path (cells detach irreversibly, all boundary cells above
-    sigma_c at once), so the search moves the way a slowly released load does: every
-    trial starts from the last state whose force is still above the target, and no
-    step lowers the depth by more than ``max_step``.  Per target F_t: steps downward
-    (secant-sized) until F(d) <= F_t, then false position (Illinois) between the last
-    state above and the trial below until |F - F_t| <= rtol * max(|F_t|, |F0|).  A
-    step whose force rose (a detachment event) is passed through like any state above
-    the target.  A step that loses the whole contact is halved towards the last state;
-    when ``max_halvings`` halvings in a row still lose it, the contact cannot carry
-    F_t: under force control the indenter jumps off.  ``stiffness`` (dF/dd > 0) sizes
-    the first step.
-
-    Returns (records, jumped): one record per reached target (target, d, force,
-    n_contact, trials) and whether the jump-off was reached before the targets ran out.
-    Raises RuntimeError if a target takes more than ``max_trials`` steps.
-    """
-    d, state, F, k = float(d0), state0, float(F0), float(stiffness)
-    out = []
-    for Ft in forces:
-        Ft = float(Ft)
-        if not Ft < F:
-            raise ValueError("force targets must decrease below the current force")
-        scale = rtol * max(abs(Ft), abs(F0))
-        hi = [d, F, state]                  # last state with F > Ft: every trial starts here
-        f_hi = F                            # its force as false position sees it (Illinois-scaled)
-        lo = None                           # trial below the target: (d, F as scaled)
-        side = 0
-        dn = d - min((F - Ft) / k, max_step)
-        halvings, trials, done = 0, 0, None
-        while True:
-            if trials >= max_trials:
-                raise RuntimeError(f"force target {Ft} not reached in {max_trials} steps")
-            st, Fn, nc = solve_depth(dn, hi[2])
-            trials += 1
-            if nc == 0:
-                halvings += 1
-                if halvings > max_halvings:
-                    break
-                dn = 0.5 * (hi[0] + dn)
-                continue
-            halvings = 0
-            if abs(Fn - Ft) <= scale:
-                done = (dn, Fn, st, nc)
-                break
-            if Fn > Ft:
-                if lo is None:              # still above the target: move on down the branch
-                    if Fn < hi[1]:
-                        k = (hi[1] - Fn) / (hi[0] - dn)
-                    hi, f_hi = [dn, Fn, st], Fn
-                    dn = dn - min((Fn - Ft) / k, max_step)
-                    continue
-                hi, f_hi = [dn, Fn, st], Fn
-                if side == 1:
-                    lo = (lo[0], 0.5 * (lo[1] + Ft))
-                side = 1
-            else:
-                lo = (dn, Fn)
-                if side == -1:
-                    f_hi = 0.5 * (f_hi + Ft)
-                side = -1
-            dn = hi[0] + (Ft - f_hi) * (lo[0] - hi[0]) / (lo[1] - f_hi)
-        if done is None:
-            return out, True
-        d, F, state = float(done[0]), done[1], done[2]
-        out.append(dict(target=Ft, d=d, force=F, n_contact=done[3], trials=trials))
-    return out, False
-
-
-def force_run(kernel, height, forces, dgamma, d0, p0, mask0, F0, stiffness, tol=1e-9, max_iter=20000, rtol=2e-3,
-              max_step=np.inf, stream=None):
-    """``force_pull_off`` on the library's depth-controlled adhesive solves: the state is
-    the (pressure, contact mask) pair of the last accepted step, copied for every
-    trial.  Start from a loaded state (d0, p0, mask0, force F0), e.g. the last step of
-    ``run``.  Returns (records, jumped)."""
+def force_steps(kernel, height, forces, dgamma, p0, mask0, tol=1e-9, max_iter=20000, stream=None):
+    """Load-controlled adhesive steps with the force control inside the library: one
+    bem_solve_contact call under force control per target (in the given order), each
+    starting from the previous step's pressure and contact mask, the first from (p0,
+    mask0), e.g. the state after the last step of ``run``.  Returns (records, jumped):
+    one record per carried target (target, d, force, area, a_eq, n_contact, iters,
+    outer, status) and whether a target detached the whole area (BEM_EDETACHED: under
+    load control the indenter jumps off there)."""
     if stream is None:
         stream = torch.cuda.Stream(device=height.device)
-
-    def solve_depth(d, state):
-        p, mask = state
-        m = mask.clone()
-        p_new, res = kernel.solve(height, "depth", float(d), dgamma=dgamma, tol=tol, max_iter=max_iter,
-                                  p_init=p, contact_mask=m, stream=stream)
-        if res["status"] != 0:
-            raise RuntimeError(f"adhesive step failed: {res}")
-        return (p_new, m), res["force"], res["n_contact"]
-
+    from . import bem
+    p, mask = p0, mask0.clone()
+    out = []
     with torch.cuda.stream(stream):
-        return force_pull_off(solve_depth, forces, d0, (p0, mask0.clone()), F0, stiffness, rtol=rtol,
-                              max_step=max_step)
+        for Ft in forces:
+            m = mask.clone()
+            p_new, res = kernel.solve(height, "force", float(Ft), dgamma=dgamma, tol=tol, max_iter=max_iter,
+                                      p_init=p, contact_mask=m, stream=stream)
+            if res["status"] == bem.BEM_EDETACHED:
+                return out, True
+            out.append(dict(target=float(Ft), d=res["depth"], force=res["force"], area=res["area"],
+                            a_eq=res["a_eq"], n_contact=res["n_contact"], iters=res["iters"],
+                            outer=res["outer_iters"], status=res["status"]))
+            p, mask = p_new, m
+    return out, False

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import analytic, kernel as okernel
+from oracle import analytic, contact, kernel as okernel, operator
 from paper_1807_01885_gb300 import bem, inputs, ramp
 
 pytestmark = pytest.mark.gpu
@@ -150,13 +150,67 @@ def test_ramp_resume_repeats_trajectory(cuda, tmp_path):
         assert a["force"] == b["force"]
 
 
-def test_force_controlled_pull_off_jkr(cuda):
-    """Force control (the variant beside the displacement control of Sec. 2): E1 = E2,
-    jump-off radius 16 cells.  Loaded by depth, then released target by target; every
-    target is met by the library's depth-controlled adhesive steps to the search
-    tolerance, the indenter jumps off at the first target below the force minimum of
-    the same branch followed in small depth steps, and that force is the JKR pull-off
-    force -(3/2) pi R dgamma (Eqs. 22/23 at epsilon = 0) within 6 %."""
+def _jkr_oracle_loaded(N):
+    """JKR sphere (E1 = E2, jump-off radius 5 cells), loaded by the oracle's
+    displacement-controlled steps: (mv, f, delta, E, nu, dgamma, sigma_c, last state)."""
+    R, E, nu = 1.0, 1.0, 0.3
+    delta = 0.5 / N
+    Es = okernel.e_star(E, nu)
+    a_d = 5 * delta
+    dg = a_d ** 3 * 8 * Es / (np.pi * R * R)
+    Kg = operator.khat_grid(N, delta, np.inf, E, nu, E, nu, 0)
+    mv = lambda p: operator.matvec_fft(Kg, p)
+    f = inputs.sphere_height(N, delta, R)
+    sc = contact.sigma_c(E, nu, dg, delta)
+    d_max = (1.4 * 9 ** (1 / 3) * a_d) ** 2 / R
+    last = contact.adhesive_ramp(mv, f, delta, np.linspace(0, d_max, 6), sc, tol=1e-12)[-1]
+    return mv, f, delta, E, nu, dg, sc, last
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_force_controlled_adhesive_step_matches_oracle(cuda, precision):
+    """Load control inside the library (every fixed-area CG of the Sec. 2 procedure
+    carries the force, d its multiplier) against the oracle's load-controlled step
+    (superposition of two fixed-area solves): from the same loaded state, an unloading
+    target and a tensile one give the same contact area cell for cell, the same
+    pressure and depth, and the target force."""
+    N = 32
+    mv, f, delta, E, nu, dg, sc, last = _jkr_oracle_loaded(N)
+    Fj = analytic.jkr_pull_off_force(1.0, dg)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol, tp, td = (1e-12, 1e-9, 1e-9) if precision == "fp64" else (1e-7, 2e-4, 2e-5)
+    with bem.Kernel(N, delta, np.inf, E, nu, E, nu, precision=precision) as k:
+        for F in (0.5 * last["force"], 0.5 * Fj):
+            p_o, C_o, d_o, _, _ = contact.adhesive_step_force(mv, f, F, delta, last["C"], sc, tol=1e-13)
+            mask = torch.tensor(last["C"].astype(np.uint8), device=cuda)
+            p, res = k.solve(torch.tensor(f, dtype=dt, device=cuda), "force", F, dgamma=dg, tol=tol,
+                             p_init=torch.tensor(last["p"], dtype=dt, device=cuda), contact_mask=mask)
+            assert res["status"] == 0
+            assert np.array_equal(mask.cpu().numpy().astype(bool), C_o)
+            p = p.double().cpu().numpy()
+            assert np.linalg.norm(p - p_o) / np.linalg.norm(p_o) < tp
+            assert res["depth"] == pytest.approx(d_o, rel=td)
+            assert res["force"] == pytest.approx(F, rel=10 * tp)
+
+
+def test_force_controlled_adhesive_needs_a_contact_area(cuda):
+    N = 32
+    f = torch.tensor(inputs.sphere_height(N, 1.0 / N, 1.0), device=cuda)
+    with bem.Kernel(N, 1.0 / N, np.inf, 1.0, 0.3, 1.0, 0.3) as k:
+        with pytest.raises(bem.BemError) as e:
+            k.solve(f, "force", -1e-4, dgamma=1e-3, contact_mask=torch.zeros((N, N), dtype=torch.uint8, device=cuda))
+        assert e.value.status == bem.BEM_EINVAL
+
+
+def test_library_force_controlled_pull_off_jkr(cuda):
+    """Load-controlled pull-off with the force control inside the library: E1 = E2,
+    jump-off radius 16 cells.  Loaded by depth, then targets carried one after another
+    (each step starting from the last one's pressure and area) until one detaches the
+    whole area (BEM_EDETACHED: the indenter jumps off).  Every carried step meets its
+    target; the depths decrease; the last carried force is the force minimum of the
+    same branch followed in small depth steps (within the cells by which the two paths
+    detach differently, 3 %) and the JKR pull-off force -(3/2) pi R dgamma (Eqs. 22/23
+    at epsilon = 0) within 6 %."""
     N, R, E, nu = 256, 1.0, 1.0, 0.3
     delta = 1.0 / N
     Es = okernel.e_star(E, nu)
@@ -168,20 +222,19 @@ def test_force_controlled_pull_off_jkr(cuda):
     d_end = 1.2 * analytic.jkr_jump_off(R, Es, dg)[2]
     Fj = analytic.jkr_pull_off_force(R, dg)
     spacing = 0.02 * abs(Fj)
-    rtol = 2e-3
     with bem.Kernel(N, delta, np.inf, E, nu, E, nu) as k:
         load, (p, mask) = ramp.run(k, f, np.linspace(0.0, d_max, 10), dg, tol=1e-10, with_state=True)
         F0 = load[-1]["force"]
         targets = np.concatenate([np.linspace(F0, 0.8 * Fj, 8)[1:], 0.8 * Fj - spacing * np.arange(1, 26)])
-        rec, jumped = ramp.force_run(k, f, targets, dg, d_max, p, mask, F0, 2 * load[-1]["a_eq"] * Es, tol=1e-10,
-                                     rtol=rtol, max_step=(d_max - d_end) / 90)
+        rec, jumped = ramp.force_steps(k, f, targets, dg, p, mask, tol=1e-10)
         disp = ramp.run(k, f, np.linspace(d_max, d_end, 91), dg, tol=1e-10, state=(1, p, mask))
     assert all(r["status"] == 0 for r in load + disp)
     assert jumped and 0 < len(rec) < len(targets)
     for r in rec:
-        assert abs(r["force"] - r["target"]) <= rtol * max(abs(r["target"]), F0) * (1 + 1e-9)
+        assert r["force"] == pytest.approx(r["target"], rel=1e-7, abs=1e-12)
     assert all(b["d"] < a["d"] for a, b in zip(rec, rec[1:]))
     F_min = min(r["force"] for r in disp)
     F_last = rec[-1]["force"]
     assert F_min - 0.03 * abs(Fj) <= F_last < F_min + spacing + 0.03 * abs(Fj)
     assert F_last / Fj == pytest.approx(1.0, abs=0.06)
+

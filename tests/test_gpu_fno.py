@@ -40,7 +40,9 @@ def setup(cuda, W, m, L, H, seed):
     return net, unflatten(rounded.cpu().numpy(), P)
 
 
-@pytest.mark.parametrize("W,m,L,H,B,N", [(8, 3, 2, 16, 2, 16), (32, 16, 4, 64, 1, 32), (32, 16, 4, 64, 1, 256)])
+# N = 40 leaves a ragged last tile of 16 pixels in every row of the tensor-core kernels
+@pytest.mark.parametrize("W,m,L,H,B,N", [(8, 3, 2, 16, 2, 16), (16, 5, 2, 16, 2, 40), (32, 16, 4, 64, 1, 32),
+                                         (32, 16, 4, 64, 1, 256)])
 def test_forward_matches_oracle(cuda, W, m, L, H, B, N):
     net, P = setup(cuda, W, m, L, H, seed=W)
     rng = np.random.default_rng(1)
@@ -50,6 +52,16 @@ def test_forward_matches_oracle(cuda, W, m, L, H, B, N):
     ref, _ = ofno.forward(P, x.astype(np.float64), m)
     got = out.cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-5
+    net.close()
+
+
+def test_odd_grid_is_rejected(cuda):
+    net = bem.Fno(width=8, modes=3, layers=1, hidden=8)
+    x = torch.zeros((1, 7, 15, 15), device=cuda)
+    out = torch.empty((1, 15, 15), device=cuda)
+    with pytest.raises(bem.BemError) as e:
+        net.forward(1, 15, x, out)
+    assert e.value.status == bem.BEM_EINVAL
     net.close()
 
 

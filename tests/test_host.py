@@ -295,47 +295,3 @@ def test_reference_arm_other_ranks_do_nothing(bench, monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(bench.parse())
     assert capsys.readouterr().out.strip() == "" and not calls
-
-
-def _synthetic_branch(d0, d_min=1.0, F_min=-2.0, kappa=3.0, d_jump=0.4):
-    """F(d) = F_min + kappa (d - d_min)^2 for d > d_jump, no contact below: a branch
-    whose force minimum is known exactly.  The state is the list of depths of the
-    accepted path; every call records (depth of the state it starts from, trial)."""
-    calls = []
-
-    def solve_depth(d, state):
-        calls.append((state[-1] if state else d0, d))
-        if d <= d_jump:
-            return state + [d], 0.0, 0
-        return state + [d], F_min + kappa * (d - d_min) ** 2, 10
-    return solve_depth, calls
-
-
-def test_force_pull_off_search_on_a_known_branch():
-    """Targets above the branch minimum are met to the tolerance, on the stable side
-    (d > d_min, where dF/dd > 0); the first target below the minimum ends the ramp as
-    a jump-off; every trial starts from the last accepted state's depth or below, and
-    no step exceeds max_step."""
-    from paper_1807_01885_gb300 import ramp
-    d0 = 3.0
-    solve, calls = _synthetic_branch(d0)
-    F0 = -2.0 + 3.0 * (d0 - 1.0) ** 2                   # 10.0
-    targets = [8.0, 4.0, 0.0, -1.0, -1.9, -1.99, -2.05, -3.0]
-    rec, jumped = ramp.force_pull_off(solve, targets, d0, [], F0, stiffness=12.0, rtol=1e-4, max_step=0.3)
-    assert jumped
-    assert [r["target"] for r in rec] == targets[:6]
-    for r in rec:
-        assert abs(r["force"] - r["target"]) <= 1e-4 * max(abs(r["target"]), F0)
-        assert r["d"] > 1.0                                  # the stable side of the minimum
-        exact = 1.0 + np.sqrt((r["target"] + 2.0) / 3.0)
-        assert r["d"] == pytest.approx(exact, abs=2e-3)
-    # no trial lowers the depth by more than max_step below the state it starts from
-    assert all(base - d <= 0.3 + 1e-12 for base, d in calls)
-    assert calls[0][1] < d0
-
-
-def test_force_pull_off_rejects_rising_targets():
-    from paper_1807_01885_gb300 import ramp
-    solve, _ = _synthetic_branch(3.0)
-    with pytest.raises(ValueError):
-        ramp.force_pull_off(solve, [12.0], 3.0, [], 10.0, stiffness=12.0)

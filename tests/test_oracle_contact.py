@@ -205,16 +205,34 @@ def test_adhesive_steps_are_fixed_points_of_the_rules():
     assert max(n) > 0 and n[-1] < max(n)
 
 
-def test_force_controlled_pull_off_on_oracle_steps():
-    """The force-controlled pull-off search (host logic of the package) driven by the
-    oracle's displacement-controlled adhesive steps, homogeneous JKR case (N = 64,
-    jump-off radius 5 cells): every reached target is met to the search tolerance, the
-    indenter jumps off at the first target below the force minimum of the branch
-    followed in small depth steps (to within the few cells by which the two depth
-    sequences detach differently), and that minimum is the JKR pull-off force
-    -(3/2) pi R dgamma within the discretisation error of this grid (15 %)."""
-    from paper_1807_01885_gb300 import ramp
-    N, R, E, nu = 64, 1.0, 1.0, 0.3
+def test_fixed_set_force_solves_the_bordered_system():
+    """Load control on a fixed area against brute force: the bordered (KKT) system
+    [[K_CC, -1], [1', 0]] [p_C; d] = [-f_C; F/delta^2] solved densely on an 8 x 8
+    window, a layered operator, a random area and random heights."""
+    N, delta = 8, 0.2
+    Kg, mv = _mv(N, delta, 0.3, 3.0, 0.25, 1.0, 0.4)
+    K = operator.dense_matrix(Kg)
+    rng = np.random.default_rng(11)
+    f = rng.random((N, N))
+    C = rng.random((N, N)) < 0.45
+    P = 2.5
+    c = C.reshape(-1)
+    m = int(c.sum())
+    A = np.zeros((m + 1, m + 1))
+    A[:m, :m] = K[np.ix_(c, c)]
+    A[:m, m] = -1.0
+    A[m, :m] = 1.0
+    sol = np.linalg.solve(A, np.concatenate([-f.reshape(-1)[c], [P]]))
+    p, d, _ = contact.solve_fixed_set_force(mv, C, f, P, tol=1e-14)
+    assert d == pytest.approx(sol[m], rel=1e-10)
+    np.testing.assert_allclose(p.reshape(-1)[c], sol[:m], rtol=0, atol=1e-10 * np.abs(sol[:m]).max())
+    assert np.all(p[~C] == 0.0)
+
+
+def _jkr_loaded(N=64):
+    """JKR sphere on a homogeneous half-space (jump-off radius 5 cells) after a
+    displacement-controlled loading ramp: (mv, f, delta, sigma_c, Es, dgamma, last)."""
+    R, E, nu = 1.0, 1.0, 0.3
     delta = 0.5 / N
     Es = kernel.e_star(E, nu)
     a_d = 5 * delta
@@ -224,33 +242,49 @@ def test_force_controlled_pull_off_on_oracle_steps():
     f = inputs.sphere_height(N, delta, R)
     sc = contact.sigma_c(E, nu, dg, delta)
     d_max = (1.4 * a_F) ** 2 / R
-    d_end = 1.3 * analytic.jkr_jump_off(R, Es, dg)[2]
     last = contact.adhesive_ramp(mv, f, delta, np.linspace(0, d_max, 6), sc, tol=1e-10)[-1]
-    Fj = analytic.jkr_pull_off_force(R, dg)
+    return mv, f, delta, sc, Es, dg, last, d_max
 
-    def solve_depth(d, state):
-        p, C = state
-        p2, C2, _, _ = contact.adhesive_step(mv, f, d, C, sc, p_prev=p, tol=1e-10)
-        return (p2, C2), float(delta * delta * p2.sum()), int(C2.sum())
 
+def test_load_controlled_step_is_a_fixed_point_of_the_depth_step():
+    """A load-controlled adhesive step ends in a state that the displacement-controlled
+    step at the depth it found leaves unchanged: same area after one outer pass, same
+    force, for an unloading target (half the loaded force) and a tensile one."""
+    mv, f, delta, sc, Es, dg, last, d_max = _jkr_loaded(N=32)
+    Fj = analytic.jkr_pull_off_force(1.0, dg)
+    for F in (0.5 * last["force"], 0.5 * Fj):
+        p, C, d, outer, _ = contact.adhesive_step_force(mv, f, F, delta, last["C"], sc, tol=1e-12)
+        assert delta * delta * p.sum() == pytest.approx(F, rel=1e-9)
+        assert C.any() and d < d_max
+        p2, C2, outer2, _ = contact.adhesive_step(mv, f, d, C, sc, p_prev=p, tol=1e-12)
+        assert outer2 == 1 and np.array_equal(C2, C)
+        assert delta * delta * p2.sum() == pytest.approx(F, rel=1e-8)
+
+
+def test_load_controlled_pull_off_is_jkr():
+    """Load-controlled pull-off by the oracle's own load-controlled steps (N = 64,
+    jump-off radius 5 cells): decreasing targets are carried until one detaches the
+    whole area; the last carried force is the minimum of the branch followed in small
+    depth steps (within the few cells by which the two paths detach differently, 3 %
+    of the pull-off force) and the JKR pull-off force -(3/2) pi R dgamma within this
+    grid's discretisation error (15 %)."""
+    mv, f, delta, sc, Es, dg, last, d_max = _jkr_loaded(N=64)
+    Fj = analytic.jkr_pull_off_force(1.0, dg)
     spacing = 0.05 * abs(Fj)
-    targets = np.concatenate([np.linspace(last["force"], 0.7 * Fj, 6)[1:],
-                              0.7 * Fj - spacing * np.arange(1, 15)])
-    step = (d_max - d_end) / 60
-    rec, jumped = ramp.force_pull_off(solve_depth, targets, d_max, (last["p"], last["C"]), last["force"],
-                                      2 * last["a_eq"] * Es, rtol=2e-3, max_step=step)
-    assert jumped and 0 < len(rec) < len(targets)
-    for r in rec:
-        assert abs(r["force"] - r["target"]) <= 2e-3 * max(abs(r["target"]), last["force"]) + 1e-15
-    assert all(b["d"] < a["d"] for a, b in zip(rec, rec[1:]))
+    targets = np.concatenate([np.linspace(last["force"], 0.7 * Fj, 6)[1:], 0.7 * Fj - spacing * np.arange(1, 15)])
+    C, carried, depths = last["C"], [], []
+    with pytest.raises(contact.Detached):
+        for F in targets:
+            p, C, d, _, _ = contact.adhesive_step_force(mv, f, F, delta, C, sc, tol=1e-10)
+            carried.append(F)
+            depths.append(d)
+    assert 0 < len(carried) < len(targets)
+    assert all(b < a for a, b in zip(depths, depths[1:]))
+    d_end = 1.3 * analytic.jkr_jump_off(1.0, Es, dg)[2]
     disp = contact.adhesive_ramp(mv, f, delta, np.linspace(d_max, d_end, 61)[1:], sc, C0=last["C"], tol=1e-10)
     F_min = min(o["force"] for o in disp)
-    F_last = rec[-1]["force"]
-    # the last reached target is above the branch minimum, the next one below it; the
-    # two depth sequences differ, so the cells detach in a slightly different order
-    # (3 % of the pull-off force allowed for that)
-    assert F_min - 0.03 * abs(Fj) <= F_last < F_min + spacing + 0.03 * abs(Fj)
-    assert F_last / Fj == pytest.approx(1.0, abs=0.15)
+    assert F_min - 0.03 * abs(Fj) <= carried[-1] < F_min + spacing + 0.03 * abs(Fj)
+    assert carried[-1] / Fj == pytest.approx(1.0, abs=0.15)
 
 
 def test_indefinite_operator_is_refused():
