@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--probe-matvec", type=int, default=0, metavar="K",
                     help="only run K operator products at N=2048 (FP32) and exit: the small case "
                          "that the ncu summaries under profiles/ capture")
+    ap.add_argument("--probe-fno", type=int, default=0, metavar="K",
+                    help="only run K forwards of the warm-start network (width 32, 16 modes, 4 layers) on one "
+                         "N=2048 sample and exit: the case of the network's ncu launch list")
     return ap.parse_args()
 
 
@@ -847,10 +850,29 @@ def probe_matvec(count):
     print("ok")
 
 
+def probe_fno(count):
+    """K forwards of the warm-start network on one random N = 2048 feature map; prints 'ok'."""
+    import torch
+    from paper_1807_01885_gb300 import bem, build
+    build.build()
+    net = bem.Fno(width=32, modes=16, layers=4, hidden=64)
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn((1, 7, N_GRID, N_GRID), dtype=torch.float32, device="cuda", generator=gen)
+    out = torch.empty((1, N_GRID, N_GRID), dtype=torch.float32, device="cuda")
+    for _ in range(count):
+        net.forward(1, N_GRID, x, out)
+    torch.cuda.synchronize()
+    net.close()
+    print("ok")
+
+
 def main():
     args = parse()
     if args.probe_matvec > 0:
         probe_matvec(args.probe_matvec)
+        return
+    if args.probe_fno > 0:
+        probe_fno(args.probe_fno)
         return
     if args.impl == "reference":
         run_reference(args)
