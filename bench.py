@@ -36,6 +36,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1807_01885_gb300.tuning import RadixCache  # noqa: E402  (no GPU or library needed)
+
 METRIC = "FFT-BEM matvecs/s at N=2048; time-to-converge: warm-start+batch vs plain"
 UNIT = "matvecs/s"
 N_GRID = 2048
@@ -271,25 +273,6 @@ def profiled_traffic():
     if fields.get("source_sha256") != h.hexdigest():
         return None
     return int(fields["traffic_bytes_per_launch"])
-
-
-class RadixCache:
-    """FFT radix per grid size, picked by the library's autotuner on the first kernel
-    of that size and applied to the later ones."""
-
-    def __init__(self, fixed=None):
-        self.choice = {}
-        self.fixed = fixed
-
-    def apply(self, k, stream=None):
-        if self.fixed is not None:
-            k.set_radix(*self.fixed, stream=stream)
-            self.choice[k.N] = tuple(self.fixed)
-        elif k.N not in self.choice:
-            self.choice[k.N] = k.autotune(reps=5, stream=stream)
-        else:
-            k.set_radix(*self.choice[k.N], stream=stream)
-        return self.choice[k.N]
 
 
 def make_instances(torch, dev, bem, inputs, radix):

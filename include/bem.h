@@ -283,6 +283,14 @@ int64_t bem_fno_param_count(bem_fno f);
 bem_status bem_fno_set_params(bem_fno f, const float* params, int64_t count, void* cuda_stream);
 /* copy out the float masters (rounded = 0) or the bfloat16 values in use (rounded = 1) */
 bem_status bem_fno_get_params(bem_fno f, float* params, int64_t count, int32_t rounded, void* cuda_stream);
+/* Adam's state for checkpoints: the first and second moment vectors (count floats
+ * each, host or device) and the number of steps taken.  Restore a checkpoint with
+ * bem_fno_set_params (which clears the state) followed by bem_fno_set_state; the
+ * next training step then equals the one the saved network would have taken.
+ * BEM_EINVAL for a NULL argument, a wrong count or step < 0. */
+bem_status bem_fno_get_state(bem_fno f, float* m1, float* m2, int64_t count, int32_t* step, void* cuda_stream);
+bem_status bem_fno_set_state(bem_fno f, const float* m1, const float* m2, int64_t count, int32_t step,
+                             void* cuda_stream);
 /* features of B samples: heights [B][N][N]; params [B][4] doubles (h/delta, E1/E2, nu1,
  * nu2) -> x [B][7][N][N]: height standardised per sample, log(h/delta)/log 200,
  * log(E1/E2)/log 20, nu1, nu2, (column + 1/2)/N, (row + 1/2)/N.  B <= 4096. */

@@ -30,7 +30,8 @@ BEM_OP_PERIODIC, BEM_OP_OPEN = 0, 1
 EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
            "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_set_pass_timing", "bem_pass_timing",
            "bem_launch_count", "bem_last_error", "bem_version", "bem_fno_create", "bem_fno_destroy",
-           "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features", "bem_fno_forward",
+           "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_get_state",
+           "bem_fno_set_state", "bem_fno_features", "bem_fno_forward",
            "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure", "bem_set_radix",
            "bem_autotune", "bem_make_kernel_layers", "bem_rebuild_kernel")
 BEM_MAX_LAYERS = 8
@@ -118,13 +119,16 @@ def load(path=None):
     lib.bem_fno_param_count.restype = i64
     lib.bem_fno_set_params.argtypes = [vp, vp, i64, vp]
     lib.bem_fno_get_params.argtypes = [vp, vp, i64, i32, vp]
+    lib.bem_fno_get_state.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i32), vp]
+    lib.bem_fno_set_state.argtypes = [vp, vp, vp, i64, i32, vp]
     lib.bem_fno_features.argtypes = [vp, i32, i32, vp, vp, vp, vp]
     lib.bem_fno_forward.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.bem_fno_gradients.argtypes = [vp, i32, i32, vp, vp, vp, dbl, vp]
     lib.bem_fno_train_step.argtypes = [vp, i32, i32, vp, vp, ctypes.c_float, dbl, vp]
     lib.bem_fno_target.argtypes = [vp, i32, i32, vp, vp, vp, vp]
     lib.bem_fno_pressure.argtypes = [vp, i32, i32, vp, vp, ctypes.c_float, vp, vp]
-    for name in ("bem_fno_create", "bem_fno_destroy", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_features",
+    for name in ("bem_fno_create", "bem_fno_destroy", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_get_state",
+                 "bem_fno_set_state", "bem_fno_features",
                  "bem_fno_forward", "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure"):
         getattr(lib, name).restype = i32
     lib.bem_set_pass_timing.argtypes = [vp, i32]
@@ -404,6 +408,30 @@ class Fno:
     def get_params(self, out, rounded=False, stream=None):
         _check(load().bem_fno_get_params(self.handle, _ptr(out), self.count, 1 if rounded else 0, _stream(stream)))
         return out
+
+    def save(self, path):
+        """Checkpoint: the float master parameters, Adam's moments and step count, and the
+        network's sizes, in one .npz file."""
+        w, m1, m2 = (np.empty(self.count, dtype=np.float32) for _ in range(3))
+        self.get_params(w)
+        step = ctypes.c_int32()
+        _check(load().bem_fno_get_state(self.handle, _ptr(m1), _ptr(m2), self.count, ctypes.byref(step), None))
+        d = self.desc
+        np.savez(path, desc=np.array([d.width, d.modes, d.layers, d.hidden], dtype=np.int64), params=w, m1=m1, m2=m2,
+                 step=np.int64(step.value))
+
+    @classmethod
+    def load(cls, path):
+        """A network restored from ``save``: the same parameters and optimiser state."""
+        z = np.load(path)
+        width, modes, layers, hidden = (int(v) for v in z["desc"])
+        net = cls(width=width, modes=modes, layers=layers, hidden=hidden)
+        w = np.ascontiguousarray(z["params"], dtype=np.float32)
+        m1 = np.ascontiguousarray(z["m1"], dtype=np.float32)
+        m2 = np.ascontiguousarray(z["m2"], dtype=np.float32)
+        net.set_params(w)
+        _check(load().bem_fno_set_state(net.handle, _ptr(m1), _ptr(m2), net.count, int(z["step"]), None))
+        return net
 
     def features(self, B, N, heights, params, x, stream=None):
         _check(load().bem_fno_features(self.handle, B, N, _ptr(heights), _ptr(params), _ptr(x), _stream(stream)))

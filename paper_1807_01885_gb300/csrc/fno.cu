@@ -1690,6 +1690,33 @@ bem_status bem_fno_get_params(bem_fno f, float* w, int64_t count, int32_t rounde
   return BEM_OK;
 }
 
+bem_status bem_fno_get_state(bem_fno f, float* m1, float* m2, int64_t count, int32_t* step, void* cuda_stream) {
+  if (f == nullptr || m1 == nullptr || m2 == nullptr || step == nullptr || count != (int64_t)f->P) {
+    set_error("bad optimiser state arguments");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  BEM_CUDA_TRY(cudaMemcpyAsync(m1, f->m1, f->P * sizeof(float), cudaMemcpyDefault, s));
+  BEM_CUDA_TRY(cudaMemcpyAsync(m2, f->m2, f->P * sizeof(float), cudaMemcpyDefault, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  *step = f->step;
+  return BEM_OK;
+}
+
+bem_status bem_fno_set_state(bem_fno f, const float* m1, const float* m2, int64_t count, int32_t step,
+                             void* cuda_stream) {
+  if (f == nullptr || m1 == nullptr || m2 == nullptr || count != (int64_t)f->P || step < 0) {
+    set_error("bad optimiser state arguments");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  BEM_CUDA_TRY(cudaMemcpyAsync(f->m1, m1, f->P * sizeof(float), cudaMemcpyDefault, s));
+  BEM_CUDA_TRY(cudaMemcpyAsync(f->m2, m2, f->P * sizeof(float), cudaMemcpyDefault, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  f->step = step;
+  return BEM_OK;
+}
+
 bem_status bem_fno_features(bem_fno f, int32_t B, int32_t N, const float* heights, const double* params, float* x,
                             void* cuda_stream) {
   if (f == nullptr || heights == nullptr || params == nullptr || x == nullptr || B < 1 || N < 2) {

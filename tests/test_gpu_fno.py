@@ -141,3 +141,28 @@ def test_warm_start_gain(cuda):
     print(f"warm-start iterations {it_warm.mean():.1f} vs cold {it_cold.mean():.1f}")
     assert it_warm.mean() <= 0.9 * it_cold.mean()
     net.close()
+
+
+def test_checkpoint_restores_training(cuda, tmp_path):
+    """A saved network (parameters, Adam moments, step count) continues training
+    exactly as the original: the step after the restore equals the original's, bit
+    for bit."""
+    net, _ = setup(cuda, 8, 3, 2, 16, seed=5)
+    rng = np.random.default_rng(6)
+    x = torch.tensor(rng.standard_normal((2, 7, 16, 16)).astype(np.float32), device=cuda)
+    t = torch.tensor(rng.standard_normal((2, 16, 16)).astype(np.float32), device=cuda)
+    for _ in range(3):
+        net.train_step(2, 16, x, t, 1e-3)
+    path = str(tmp_path / "fno.npz")
+    net.save(path)
+    twin = bem.Fno.load(path)
+    la = net.train_step(2, 16, x, t, 1e-3)
+    lb = twin.train_step(2, 16, x, t, 1e-3)
+    assert la == lb
+    wa = torch.empty(net.count, dtype=torch.float32, device=cuda)
+    wb = torch.empty(twin.count, dtype=torch.float32, device=cuda)
+    net.get_params(wa)
+    twin.get_params(wb)
+    assert torch.equal(wa, wb)
+    net.close()
+    twin.close()

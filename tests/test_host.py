@@ -201,6 +201,27 @@ def test_radix_cache_tunes_once_per_size(bench):
     assert fixed.apply(d) == (4, 4) and d.calls == [("set", 4, 4)]
 
 
+def test_radix_cache_file_is_reused(tmp_path):
+    """An on-disk cache tunes a (device, N, precision) once across processes: a second
+    cache reading the same file applies the stored choice without timing."""
+    from paper_1807_01885_gb300 import tuning
+    path = str(tmp_path / "sub" / "radix.json")
+    first = tuning.RadixCache(path=path, device="GB300")
+    a = _FakeKernel(2048)
+    assert first.apply(a) == (4, 3) and a.calls == [("tune",)]
+    second = tuning.RadixCache(path=path, device="GB300")
+    b = _FakeKernel(2048)
+    assert second.apply(b) == (4, 3) and b.calls == [("set", 4, 3)]
+    other = tuning.RadixCache(path=path, device="B200")
+    c = _FakeKernel(2048)
+    assert other.apply(c) == (4, 3) and c.calls == [("tune",)]
+    with open(path, "w") as fh:
+        fh.write("not json")
+    broken = tuning.RadixCache(path=path, device="GB300")
+    d = _FakeKernel(2048)
+    assert broken.apply(d) == (4, 3) and d.calls == [("tune",)]
+
+
 def test_bench_defaults(bench, monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
