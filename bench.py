@@ -250,7 +250,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-PROFILE = os.path.join(ROOT, "profiles", "col_pass_N2048_fp32.md")
+PROFILE = os.path.join(ROOT, "profiles", "col_pass_pair_N2048_fp32.md")
 # the sources of the three FFT passes (the column pass, its FFT and its launch);
 # a change to any of them invalidates the captured traffic
 PROFILED_SOURCES = ["paper_1807_01885_gb300/csrc/matvec_reg.cuh", "paper_1807_01885_gb300/csrc/fft_reg.cuh",
@@ -784,7 +784,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm,
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
                      "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "traffic_source": "profiles/col_pass_N2048_fp32.md (ncu, cold cache)" if traffic else None,
+                     "traffic_source": "profiles/col_pass_pair_N2048_fp32.md (ncu, cold cache)" if traffic else None,
                      "alg_bytes_per_launch": rb[dom]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N_GRID * N_GRID,
                 "d2h_bytes_per_step": 4 * N_GRID * N_GRID + 96},

@@ -170,6 +170,17 @@ bem_status bem_rebuild_kernel(bem_kernel k, const bem_kernel_desc* desc, void* c
  * (host or device).  Entry (0,0) is the DC value chosen by dc_mode. */
 bem_status bem_kernel_table(bem_kernel k, void* out, void* cuda_stream);
 
+/* Workspace guard check (a debugging aid, not part of the method): every large array
+ * of the handle's workspace (spectrum, tables, twiddles, solver vectors, masks,
+ * partial sums, staging) sits between two 256-byte zones of a fixed byte pattern;
+ * *bad_bytes receives the number of zone bytes that no longer hold it (0 unless a
+ * kernel wrote outside an array).  Synchronises the stream.
+ * bem_debug_poke_guard overwrites one byte of the zone after array i (0 <= i < the
+ * number of guarded arrays; BEM_EINVAL otherwise) with a host-side memset: fault
+ * injection for testing the check, no kernel runs. */
+bem_status bem_check_guards(bem_kernel k, int64_t* bad_bytes, void* cuda_stream);
+bem_status bem_debug_poke_guard(bem_kernel k, int32_t i);
+
 /* u = K p (Eq. 1 evaluated by Eq. 11).  p and u: N*N, host or device.  Device
  * arguments: asynchronous on the stream.  Host arguments: returns after u is written. */
 bem_status bem_matvec(bem_kernel k, const void* p, void* u, void* cuda_stream);

@@ -30,7 +30,7 @@ BEM_OP_PERIODIC, BEM_OP_OPEN = 0, 1
 EXPORTS = ("bem_make_kernel", "bem_destroy_kernel", "bem_kernel_table", "bem_matvec", "bem_solve_contact",
            "bem_solve_batch", "bem_matvec_static", "bem_profile_passes", "bem_set_pass_timing", "bem_pass_timing",
            "bem_launch_count", "bem_last_error", "bem_version", "bem_fno_create", "bem_fno_destroy",
-           "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_get_state",
+           "bem_check_guards", "bem_debug_poke_guard", "bem_fno_param_count", "bem_fno_set_params", "bem_fno_get_params", "bem_fno_get_state",
            "bem_fno_set_state", "bem_fno_features", "bem_fno_forward",
            "bem_fno_gradients", "bem_fno_train_step", "bem_fno_target", "bem_fno_pressure", "bem_set_radix",
            "bem_autotune", "bem_make_kernel_layers", "bem_rebuild_kernel")
@@ -97,6 +97,10 @@ def load(path=None):
     lib.bem_rebuild_kernel.restype = i32
     lib.bem_destroy_kernel.argtypes = [vp]
     lib.bem_kernel_table.argtypes = [vp, vp, vp]
+    lib.bem_check_guards.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), vp]
+    lib.bem_check_guards.restype = i32
+    lib.bem_debug_poke_guard.argtypes = [vp, i32]
+    lib.bem_debug_poke_guard.restype = i32
     lib.bem_matvec.argtypes = [vp, vp, vp, vp]
     lib.bem_solve_contact.argtypes = [vp, ctypes.POINTER(Problem), vp, ctypes.POINTER(Result), vp]
     lib.bem_solve_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Problem), ctypes.POINTER(vp),
@@ -366,6 +370,13 @@ class Kernel:
         bem_rebuild_kernel(self.handle, self.N, delta, h, E1, nu1, E2, nu2, prec, dc_mode, stream, op_kind)
         self.delta = delta
         self.params = dict(h=h, E1=E1, nu1=nu1, E2=E2, nu2=nu2)
+
+    def check_guards(self, stream=None):
+        """Bytes of the workspace guard zones that lost their pattern (0: no kernel wrote
+        outside its arrays)."""
+        bad = ctypes.c_int64()
+        _check(load().bem_check_guards(self.handle, ctypes.byref(bad), _stream(stream)))
+        return bad.value
 
     def set_radix(self, rows, cols, stream=None):
         """log2 of the FFT radix of the row and column passes (3 or 4; 3 only in fp64)."""

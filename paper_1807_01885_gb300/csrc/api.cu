@@ -148,25 +148,40 @@ struct DeviceGuard {
   }
 };
 
+// A workspace array with guard zones on both sides (see kGuard).
+template <typename P>
+cudaError_t alloc_guarded(Workspace& w, P** p, size_t bytes) {
+  if (w.n_guards >= kMaxGuarded) return cudaErrorInvalidValue;
+  unsigned char* base = nullptr;
+  cudaError_t e = cudaMalloc((void**)&base, bytes + 2 * kGuard);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemset(base, kGuardByte, kGuard)) != cudaSuccess ||
+      (e = cudaMemset(base + kGuard + bytes, kGuardByte, kGuard)) != cudaSuccess) {
+    cudaFree(base);
+    return e;
+  }
+  w.guards[w.n_guards++] = GuardRec{base, bytes};
+  *p = reinterpret_cast<P*>(base + kGuard);
+  return cudaSuccess;
+}
+
+__global__ void k_guard_scan(const unsigned char* __restrict__ lead, const unsigned char* __restrict__ trail,
+                             unsigned long long* bad) {
+  const unsigned i = threadIdx.x;   // one thread per guard byte pair
+  unsigned n = 0;
+  if (i < kGuard) n = (lead[i] != kGuardByte) + (trail[i] != kGuardByte);
+  if (n) atomicAdd(bad, (unsigned long long)n);
+}
+
 void free_ws(bem_kernel_s* k) {
   Workspace& w = k->ws;
-  cudaFree(w.spec);
-  cudaFree(w.table);
-  cudaFree(w.table64);
-  cudaFree(w.tw);
-  cudaFree(w.twr);
-  cudaFree(w.twc);
-  cudaFree(w.twpc);
-  cudaFree(w.vec);
-  cudaFree(w.mask);
-  cudaFree(w.partials);
+  for (int i = 0; i < w.n_guards; ++i) cudaFree(w.guards[i].base);
+  cudaFree(w.guard_bad);
   cudaFree(w.ticket);
   cudaFree(w.state);
   cudaFreeHost(w.state_host);
   cudaFreeHost(w.aux_host);
   if (w.done_ev != nullptr) cudaEventDestroy(w.done_ev);
-  cudaFree(w.stage_in);
-  cudaFree(w.stage_out);
   w = Workspace{};
 }
 
@@ -434,23 +449,25 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
     return r;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&w.spec, spec_bytes(k))) != cudaSuccess) return fail(e, "cudaMalloc(spec)");
-  if ((e = cudaMalloc(&w.table, table_bytes(k))) != cudaSuccess) return fail(e, "cudaMalloc(table)");
-  if ((e = cudaMalloc((void**)&w.table64, (size_t)(k->N + 1) * (k->N + 1) * sizeof(double))) != cudaSuccess)
+  if ((e = alloc_guarded(w, &w.spec, spec_bytes(k))) != cudaSuccess) return fail(e, "cudaMalloc(spec)");
+  if ((e = alloc_guarded(w, &w.table, table_bytes(k))) != cudaSuccess) return fail(e, "cudaMalloc(table)");
+  if ((e = alloc_guarded(w, &w.table64, (size_t)(k->N + 1) * (k->N + 1) * sizeof(double))) != cudaSuccess)
     return fail(e, "cudaMalloc(table64)");
-  if ((e = cudaMalloc(&w.tw, (size_t)k->M * 2 * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(tw)");
-  if ((e = cudaMalloc(&w.twr, (size_t)stage_tw_count(k->logN) * 2 * k->elem)) != cudaSuccess)
+  if ((e = alloc_guarded(w, &w.tw, (size_t)k->M * 2 * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(tw)");
+  if ((e = alloc_guarded(w, &w.twr, (size_t)stage_tw_count(k->logN) * 2 * k->elem)) != cudaSuccess)
     return fail(e, "cudaMalloc(twr)");
-  if ((e = cudaMalloc(&w.twc, (size_t)stage_tw_count(k->logN + 1) * 2 * k->elem)) != cudaSuccess)
+  if ((e = alloc_guarded(w, &w.twc, (size_t)stage_tw_count(k->logN + 1) * 2 * k->elem)) != cudaSuccess)
     return fail(e, "cudaMalloc(twc)");
   if (k->prec == BEM_FP32 &&
-      (e = cudaMalloc(&w.twpc, (size_t)pair_tw_count(k->logN + 1) * 4 * sizeof(float))) != cudaSuccess)
+      (e = alloc_guarded(w, &w.twpc, (size_t)pair_tw_count(k->logN + 1) * 4 * sizeof(float))) != cudaSuccess)
     return fail(e, "cudaMalloc(twpc)");
-  if ((e = cudaMalloc(&w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
-  if ((e = cudaMalloc((void**)&w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
-  if ((e = cudaMalloc((void**)&w.partials, 16 * 2048 * sizeof(double))) != cudaSuccess)
+  if ((e = alloc_guarded(w, &w.vec, 7 * n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(vec)");
+  if ((e = alloc_guarded(w, &w.mask, 2 * n)) != cudaSuccess) return fail(e, "cudaMalloc(mask)");
+  if ((e = alloc_guarded(w, &w.partials, 16 * 2048 * sizeof(double))) != cudaSuccess)
     return fail(e, "cudaMalloc(partials)");
   if ((e = cudaMalloc((void**)&w.ticket, sizeof(unsigned int))) != cudaSuccess) return fail(e, "cudaMalloc(ticket)");
+  if ((e = cudaMalloc((void**)&w.guard_bad, sizeof(unsigned long long))) != cudaSuccess)
+    return fail(e, "cudaMalloc(guard counter)");
   if ((e = cudaMalloc((void**)&w.state, sizeof(SolveState))) != cudaSuccess) return fail(e, "cudaMalloc(state)");
   if ((e = cudaMallocHost((void**)&w.state_host, sizeof(SolveState))) != cudaSuccess)
     return fail(e, "cudaMallocHost(state)");
@@ -458,8 +475,8 @@ static bem_status make_kernel(const bem_kernel_desc* desc, int32_t n_layers, con
     return fail(e, "cudaMallocHost(aux)");
   if ((e = cudaEventCreateWithFlags(&w.done_ev, cudaEventDisableTiming)) != cudaSuccess)
     return fail(e, "cudaEventCreate");
-  if ((e = cudaMalloc(&w.stage_in, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_in)");
-  if ((e = cudaMalloc(&w.stage_out, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_out)");
+  if ((e = alloc_guarded(w, &w.stage_in, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_in)");
+  if ((e = alloc_guarded(w, &w.stage_out, n * k->elem)) != cudaSuccess) return fail(e, "cudaMalloc(stage_out)");
   if ((e = cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(e, "memset(ticket)");
   st = build_table(k, s);
   if (st != BEM_OK) {
@@ -520,6 +537,39 @@ bem_status bem_destroy_kernel(bem_kernel k) {
   }
   free_ws(k);
   delete k;
+  return BEM_OK;
+}
+
+bem_status bem_check_guards(bem_kernel k, int64_t* bad_bytes, void* cuda_stream) {
+  if (k == nullptr || bad_bytes == nullptr) {
+    set_error("NULL kernel or output");
+    return BEM_EINVAL;
+  }
+  DeviceGuard dg(k->dev);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Workspace& w = k->ws;
+  BEM_CUDA_TRY(cudaMemsetAsync(w.guard_bad, 0, sizeof(unsigned long long), s));
+  for (int i = 0; i < w.n_guards; ++i) {
+    const GuardRec& g = w.guards[i];
+    k_guard_scan<<<1, (unsigned)kGuard, 0, s>>>(g.base, g.base + kGuard + g.bytes, w.guard_bad);
+  }
+  note_launches(w.n_guards);
+  BEM_CUDA_TRY(cudaGetLastError());
+  unsigned long long bad = 0;
+  BEM_CUDA_TRY(cudaMemcpyAsync(&bad, w.guard_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA_TRY(cudaStreamSynchronize(s));
+  *bad_bytes = (int64_t)bad;
+  return BEM_OK;
+}
+
+bem_status bem_debug_poke_guard(bem_kernel k, int32_t i) {
+  if (k == nullptr || i < 0 || i >= k->ws.n_guards) {
+    set_error("no such guarded array");
+    return BEM_EINVAL;
+  }
+  DeviceGuard dg(k->dev);
+  const GuardRec& g = k->ws.guards[i];
+  BEM_CUDA_TRY(cudaMemset(g.base + kGuard + g.bytes, 0, 1));
   return BEM_OK;
 }
 

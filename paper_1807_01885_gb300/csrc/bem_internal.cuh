@@ -118,6 +118,17 @@ struct SolveState {
 };
 
 // Workspace owned by a kernel handle.
+// Guard zones: every large workspace array is allocated with kGuard bytes of the
+// pattern kGuardByte before and after it (the payload keeps the allocation's 256-byte
+// alignment); bem_check_guards counts the guard bytes that no longer hold it.
+constexpr size_t kGuard = 256;
+constexpr unsigned char kGuardByte = 0xB5;
+constexpr int kMaxGuarded = 16;
+struct GuardRec {
+  unsigned char* base = nullptr;   // start of the allocation (leading guard)
+  size_t bytes = 0;                // payload size
+};
+
 struct Workspace {
   void* spec = nullptr;      // (N/TC + 1) * N * TC complex
   void* table = nullptr;     // K^/M^2 in the path precision: N >= 16 (N+1) rows of N+4 (row j = column j), else blocked
@@ -136,6 +147,9 @@ struct Workspace {
   cudaEvent_t done_ev = nullptr;      // batch rounds: state copied back
   void* stage_in = nullptr;  // staging for host arguments (N*N)
   void* stage_out = nullptr;
+  GuardRec guards[kMaxGuarded];      // the guarded allocations (all of the arrays above but ticket and state)
+  int n_guards = 0;
+  unsigned long long* guard_bad = nullptr;   // device counter of bem_check_guards
 };
 
 }  // namespace bem

@@ -660,20 +660,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int PENDING>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
 
-// The fused layer for N a multiple of 16, with the activations of the next y-tile
-// copied to shared memory (cp.async, two stages per warp) while the current one is
-// contracted: each warp stages its W channels x 16 pixels (W 64-byte rows, row stride
-// 20 floats, which makes the fragment reads conflict-free).  Same arithmetic and
-// order as k_layer_tc.
-constexpr int kLayerRow = 20;
+// The fused layer for N a multiple of 16, with the activations of the next y-tiles
+// copied to shared memory (cp.async, kLayerStages stages per warp: up to three tiles
+// in flight while one is contracted): each warp stages its W channels x 16 pixels (W
+// 64-byte rows, row stride 20 floats, which makes the fragment reads conflict-free).
+// Same arithmetic and order as k_layer_tc.
+constexpr int kLayerRow = 20, kLayerStages = 4;
 template <int KT, int NT, int KS>
 __global__ void __launch_bounds__(128, 4) k_layer_tc_pipe(const float* __restrict__ V, const bf16* __restrict__ Ww,
                                                        const bf16* __restrict__ bias, const float* __restrict__ A,
                                                        const float* __restrict__ cs, const uint4* __restrict__ TfA,
                                                        float* __restrict__ Z, float* __restrict__ Vout, int N, int n2m,
                                                        size_t rows, int tpw, int gelu) {
-  constexpr int W = 8 * NT, STAGE = W * kLayerRow;
-  __shared__ __align__(16) float sbuf[4][2][STAGE];
+  constexpr int W = 8 * NT, STAGE = W * kLayerRow, S = kLayerStages;
+  __shared__ __align__(16) float sbuf[4][S][STAGE];
   const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4, wid = threadIdx.x / 32;
   const int YT = N / 16, chunks = (YT + tpw - 1) / tpw;
   const size_t w = (size_t)blockIdx.x * 4 + wid;
@@ -733,14 +733,21 @@ __global__ void __launch_bounds__(128, 4) k_layer_tc_pipe(const float* __restric
     cp_async_commit();
   };
   const int yt0 = chunk * tpw, yt1 = min(YT, yt0 + tpw);
-  if (yt0 < yt1) prefetch(yt0, 0);
-  int st = 0;
-  for (int yt = yt0; yt < yt1; ++yt) {
-    if (yt + 1 < yt1) prefetch(yt + 1, st ^ 1);
+  // one commit group per tile (empty past the chunk's end): before the contraction of
+  // tile yt0 + i, S + i groups are committed and waiting until at most S - 1 are
+  // pending completes the first i + 1
+#pragma unroll
+  for (int i = 0; i < S - 1; ++i) {
+    if (yt0 + i < yt1) prefetch(yt0 + i, i);
     else cp_async_commit();
-    cp_async_wait<1>();
+  }
+  for (int yt = yt0; yt < yt1; ++yt) {
+    const int i = yt - yt0;
+    if (yt + S - 1 < yt1) prefetch(yt + S - 1, (i + S - 1) % S);
+    else cp_async_commit();
+    cp_async_wait<S - 1>();
     __syncwarp();
-    const float* sb = buf[st];
+    const float* sb = buf[i % S];
     const int ya = 16 * yt + g, yb = ya + 8;
     unsigned ah[KT][4], al[KT][4];
 #pragma unroll
@@ -793,7 +800,6 @@ __global__ void __launch_bounds__(128, 4) k_layer_tc_pipe(const float* __restric
         ub[oo + yb] = gelu ? gelu_f(vb2) : vb2;
       }
     }
-    st ^= 1;
   }
   cp_async_wait<0>();
 }
