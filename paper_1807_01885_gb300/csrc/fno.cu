@@ -661,11 +661,12 @@ template <int PENDING>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
 
 // The fused layer for N a multiple of 16, with the activations of the next y-tiles
-// copied to shared memory (cp.async, kLayerStages stages per warp: up to three tiles
-// in flight while one is contracted): each warp stages its W channels x 16 pixels (W
+// copied to shared memory (cp.async, kLayerStages stages per warp: the next tile in
+// flight while one is contracted; four stages measured no faster, the kernel being
+// bound by its instruction issue): each warp stages its W channels x 16 pixels (W
 // 64-byte rows, row stride 20 floats, which makes the fragment reads conflict-free).
 // Same arithmetic and order as k_layer_tc.
-constexpr int kLayerRow = 20, kLayerStages = 4;
+constexpr int kLayerRow = 20, kLayerStages = 2;
 template <int KT, int NT, int KS>
 __global__ void __launch_bounds__(128, 4) k_layer_tc_pipe(const float* __restrict__ V, const bf16* __restrict__ Ww,
                                                        const bf16* __restrict__ bias, const float* __restrict__ A,

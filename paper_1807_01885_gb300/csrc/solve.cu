@@ -335,10 +335,16 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 1) k_pk_rt(cons
   if (grid_reduce<4>(v, partials, ticket, tot)) {
     const double rbar = (st->control == BEM_CTRL_FORCE) ? tot[1] / (double)st->n_c : 0.0;
     const double den = tot[0] - rbar * tot[2];
-    double tau = tot[3] / den;
-    if (!(den > 0.0) || !isfinite(tau)) {
-      finish(st, BEM_ENAN);
-      return;
+    double tau = 0.0;
+    if (den == 0.0 && tot[3] == 0.0) {
+      // the gap is exactly level on the contact set (a symmetric set under force
+      // control): the direction is zero and no step is taken, as in the oracle
+    } else {
+      tau = tot[3] / den;
+      if (!(den > 0.0) || !isfinite(tau)) {
+        finish(st, BEM_ENAN);
+        return;
+      }
     }
     // A direction kept conjugate across a small contact-set change may fail to be
     // a descent direction; then no step is taken and the next one restarts.

@@ -105,13 +105,14 @@ def test_fig5_pull_off_force_between_limits(cuda, alpha):
         assert ratio / -2.0 == pytest.approx(1.0, abs=0.06)
 
 
-@pytest.mark.parametrize("alpha", [0.2, 15.0])
-def test_fig5_float_path_at_n1024(cuda, alpha):
+@pytest.mark.parametrize("N,alpha", [(1024, 0.2), (1024, 15.0), (2048, 0.2)])
+def test_fig5_float_path_at_large_n(cuda, N, alpha):
     """The Fig. 5 sweep's two ends on the float path (FP32 vectors and FFTs, double
-    detachment test) at N = 1024 (pull-off contact radius about 170 cells): the same
-    bounds as the FP64 runs at N = 512 (between -3/2 and -2; the thick-layer expansion
-    within 4 % at alpha = 0.2, Eq. 19 within 6 % at alpha = 15)."""
-    out, R, h, E1, nu, dg, a_ref = _fig5_ramp(cuda, alpha, N=1024, precision="fp32", tol=1e-7)
+    detachment test) at N = 1024 (pull-off contact radius about 170 cells) and the
+    thick-layer end at N = 2048 (about 340 cells): the same bounds as the FP64 runs at
+    N = 512 (between -3/2 and -2; the thick-layer expansion within 4 % at
+    alpha = 0.2, Eq. 19 within 6 % at alpha = 15)."""
+    out, R, h, E1, nu, dg, a_ref = _fig5_ramp(cuda, alpha, N=N, precision="fp32", tol=1e-7)
     assert all(r["status"] == 0 for r in out)
     assert out[-1]["n_contact"] == 0
     ratio = min(r["force"] for r in out) / (np.pi * R * dg)

@@ -337,3 +337,23 @@ def test_device_loop_equals_host_loop(cuda, control):
     assert r_dev["iters"] == r_host["iters"] and r_dev["matvecs"] == r_host["matvecs"]
     assert r_lim["status"] == bem.BEM_ENOCONV and r_lim["iters"] == lim
     assert n1 > n0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_level_gap_on_a_symmetric_contact_set(cuda, precision):
+    """Force control on a 4 x 4 window where the contact set shrinks to the four
+    symmetric centre cells: their gaps are exactly equal, the search direction is
+    zero, and the step is skipped (as in the oracle) instead of being reported as a
+    non-positive curvature."""
+    N, delta, F = 4, 0.25, 1e-4
+    f = inputs.sphere_height(N, delta, 1.0)
+    Kg = operator.khat_grid(N, delta, 0.2, 0.5, 0.3, 1.0, 0.4, 0)
+    ref = contact.solve_nonadhesive(lambda p: operator.matvec_fft(Kg, p), f, delta, "force", F, tol=1e-12)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    with bem.Kernel(N, delta, 0.2, 0.5, 0.3, 1.0, 0.4, precision=precision) as k:
+        p, res = k.solve(torch.tensor(f, dtype=dt, device=cuda), "force", F,
+                         tol=1e-12 if precision == "fp64" else 1e-7)
+    assert res["status"] == 0
+    assert res["n_contact"] == ref["n_contact"] == 4
+    p = p.double().cpu().numpy()
+    np.testing.assert_allclose(p, ref["p"], rtol=0, atol=(1e-10 if precision == "fp64" else 2e-4) * ref["p"].max())
