@@ -333,7 +333,7 @@ def batch_bench(torch, dev, bem, inputs, n_inst, radix):
             "batch_wall_ms": 1000 * t_batch, "sequential_wall_ms": 1000 * t_seq,
             "speedup": t_seq / t_batch, "instances_per_s": n_inst / t_batch,
             "matvecs": mv, "matvecs_per_s": mv / t_batch,
-            "fft_log2_radix": {str(n): list(radix.choice[n]) for n in sorted(sizes)},
+            "fft_log2_radix": {str(n): list(radix.by_size[n]) for n in sorted(sizes)},
             "seeds": f"{BATCH_SEED0}..{BATCH_SEED0 + n_inst - 1}"}
 
 
@@ -768,7 +768,7 @@ def run_ours(args):
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "l2": "working set ~170 MB per solve > 129 MB L2 (no flush needed); matvec-only loop cycles 8 "
                   "distinct 16.8 MB inputs",
-            "fft_log2_radix": {"rows": radix.choice[N_GRID][0], "cols": radix.choice[N_GRID][1],
+            "fft_log2_radix": {"rows": radix.by_size[N_GRID][0], "cols": radix.by_size[N_GRID][1],
                                "picked_by": "--radix" if args.radix else "bem_autotune"},
         },
         "time_to_converge_ms": ms_max / args.steps,

@@ -207,6 +207,33 @@ inline bool first_on_device(std::atomic<unsigned long long>& seen) {
 void set_error(const std::string& msg);
 // number of kernel launches issued by the library (for launch accounting)
 void note_launches(long long n);
+
+// Programmatic dependent launch along the iteration's kernel chain: a kernel launched
+// with launch_pdl may be scheduled while its predecessor's last blocks still run.
+// Every such kernel first waits for its predecessor grid (its results are then
+// visible) and then lets its own successor be scheduled, so each kernel starts only
+// after all earlier ones completed; what overlaps is the launch and block set-up with
+// the predecessor's tail.  Outside a programmatic launch both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 long long launches();
 // adds the durations of completed timed passes of k to its totals (host sync point)
 void harvest_pass_timing(const bem_kernel_s* k);

@@ -72,6 +72,7 @@ k_row_fwd_r(const T* __restrict__ p, cplx<T>* __restrict__ spec, const cplx<T>* 
   using P = Plan<LOGN, LOGR>;
   constexpr int N = 1 << LOGN, TT = P::T, SH = row_sh<LOGN, LOGR>(), R = P::R;
   constexpr int RPB = rows_per_block<T, LOGN, LOGR>();
+  pdl_enter();
   if (skip != nullptr && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* const sh0 = reinterpret_cast<C*>(smem_raw);
@@ -149,6 +150,7 @@ k_row_inv_r(const cplx<T>* __restrict__ spec, T* __restrict__ u, const cplx<T>* 
   using P = Plan<LOGN, LOGR>;
   constexpr int N = 1 << LOGN, TT = P::T, SH = row_sh<LOGN, LOGR>(), R = P::R;
   constexpr int RPB = rows_per_block<T, LOGN, LOGR>(), NT = RPB * TT;
+  pdl_enter();
   if (skip != nullptr && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* const sh0 = reinterpret_cast<C*>(smem_raw);
@@ -224,6 +226,7 @@ k_col_r(cplx<T>* __restrict__ spec, const T* __restrict__ table, const cplx<T>* 
   using P = Plan<LOGM, LOGR>;
   constexpr int M = 1 << LOGM, N = M / 2, TT = P::T, SH = P::PADL + 8, R = P::R;
   constexpr int CPB = cols_per_block<T, LOGM, LOGR>();
+  pdl_enter();
   if (skip != nullptr && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x / TT, t = threadIdx.x - c * TT;
@@ -275,6 +278,7 @@ k_col_p(float4* __restrict__ spec4, const float2* __restrict__ tab2, const float
   using pr::CP;
   constexpr int M = 1 << LOGM, N = M / 2, TT = P::T, SH = P::PADL + 8, R = P::R;
   constexpr int CPB = pairs_per_block<LOGM, LOGR>();
+  pdl_enter();
   if (skip != nullptr && *skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x / TT, t = threadIdx.x - c * TT;
@@ -383,11 +387,11 @@ struct RowLaunch {
     const size_t smem = (size_t)rpb * row_sh<LOGN, LOGR>() * sizeof(C);
     C* spec = (C*)k->ws.spec;
     if (which == 0)
-      k_row_fwd_r<T, LOGN, LOGR><<<N / rpb, rpb * PR::T, smem, s>>>(p, spec, (const C*)k->ws.twr,
-                                                                    (const C*)k->ws.tw, skip);
+      launch_pdl(k_row_fwd_r<T, LOGN, LOGR>, N / rpb, rpb * PR::T, smem, s, p, spec, (const C*)k->ws.twr,
+                 (const C*)k->ws.tw, skip);
     else
-      k_row_inv_r<T, LOGN, LOGR><<<N / rpb, rpb * PR::T, smem, s>>>(spec, u, (const C*)k->ws.twr,
-                                                                    (const C*)k->ws.tw, skip);
+      launch_pdl(k_row_inv_r<T, LOGN, LOGR>, N / rpb, rpb * PR::T, smem, s, (const C*)spec, u,
+                 (const C*)k->ws.twr, (const C*)k->ws.tw, skip);
   }
 };
 
@@ -412,15 +416,15 @@ struct ColLaunch {
       const int npairs = N / 2 + 1;
       const int grid = (npairs + ppb - 1) / ppb;
       const size_t smem = (size_t)ppb * ((PC::PADL + 8) * sizeof(pr::CP) + (N + 1) * sizeof(float2));
-      k_col_p<LOGN + 1, LOGR><<<grid, ppb * PC::T, smem, s>>>((float4*)k->ws.spec, (const float2*)k->ws.table,
-                                                             (const float4*)k->ws.twpc, npairs, skip);
+      launch_pdl(k_col_p<LOGN + 1, LOGR>, grid, ppb * PC::T, smem, s, (float4*)k->ws.spec,
+                 (const float2*)k->ws.table, (const float4*)k->ws.twpc, npairs, skip);
     } else {
       constexpr int cpb = cols_per_block<T, LOGN + 1, LOGR>();
       const int nslots = N + 1;
       const int grid = (nslots + cpb - 1) / cpb;
       const size_t smem = (size_t)cpb * (PC::PADL + 8) * sizeof(C);
-      k_col_r<T, LOGN + 1, LOGR><<<grid, cpb * PC::T, smem, s>>>((C*)k->ws.spec, (const T*)k->ws.table,
-                                                               (const C*)k->ws.twc, nslots, skip);
+      launch_pdl(k_col_r<T, LOGN + 1, LOGR>, grid, cpb * PC::T, smem, s, (C*)k->ws.spec, (const T*)k->ws.table,
+                 (const C*)k->ws.twc, nslots, skip);
     }
   }
 };

@@ -182,6 +182,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ f, T* __restrict__ dp,
                            const T* __restrict__ u, uint8_t* __restrict__ cm, double* partials,
                            unsigned int* ticket, SolveState* st, size_t n) {
+  pdl_enter();
   if (st->done) return;
   const double s = st->scale, d = st->d;
   const T dT = (T)d;
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T
 template <typename T>
 __global__ void k_pk_dir(const uint8_t* __restrict__ cm, const T* __restrict__ g, T* __restrict__ t,
                          const SolveState* st, size_t n) {
+  pdl_enter();
   if (st->done) return;
   const T gbar = (T)st->gbar, beta = (T)st->beta;
   VEC_LOOP(i4, n) {
@@ -307,6 +309,7 @@ __global__ void k_pk_dir(const uint8_t* __restrict__ cm, const T* __restrict__ g
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 1) k_pk_rt(const uint8_t* __restrict__ cm, const T* __restrict__ g, const T* __restrict__ t,
                         const T* __restrict__ r, double* partials, unsigned int* ticket, SolveState* st, size_t n) {
+  pdl_enter();
   if (st->done) return;
   const T gbar = (T)st->gbar;
   Acc<T> art, ar, at, agt;
@@ -365,6 +368,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_update(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
                             T* __restrict__ dp, const T* __restrict__ f, double* partials, unsigned int* ticket,
                             SolveState* st, size_t n) {
+  pdl_enter();
   if (st->done) return;
   const T tau = (T)st->tau;
   const bool replace = st->replace != 0;
@@ -524,6 +528,7 @@ template <typename T>
 __global__ void k_lin_alpha(const T* __restrict__ s, const T* __restrict__ q, const T* __restrict__ r,
                             const uint8_t* __restrict__ C, double* partials, unsigned int* ticket, SolveState* st,
                             size_t n) {
+  pdl_enter();
   if (st->done) return;
   const bool force = st->control == BEM_CTRL_FORCE;
   Acc<T> a, aq, ar;
@@ -552,6 +557,7 @@ template <typename T>
 __global__ void k_lin_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ s, const T* __restrict__ q,
                              const uint8_t* __restrict__ C, double* partials, unsigned int* ticket, SolveState* st,
                              size_t n) {
+  pdl_enter();
   if (st->done) return;
   const T alpha = (T)st->alpha;
   const T qbar = (T)st->qbar, rbar = (T)st->lin_rbar;   // 0 under depth control
@@ -588,6 +594,7 @@ __global__ void k_lin_update(T* __restrict__ x, T* __restrict__ r, const T* __re
 template <typename T>
 __global__ void k_lin_dir(const T* __restrict__ r, T* __restrict__ s, const uint8_t* __restrict__ C,
                           const SolveState* st, size_t n) {
+  pdl_enter();
   if (st->done) return;
   const T beta = (T)st->beta;
   GRID_STRIDE(i, n) s[i] = C[i] ? r[i] + beta * s[i] : (T)0;
@@ -857,11 +864,14 @@ void pk_chunk_launches(bem_kernel_s* k, cudaStream_t s) {
   uint8_t* cm = k->ws.mask;   // contact set of the iterations (the adhesive masks are not live here)
   for (int it = 0; it < CHUNK; ++it) {
     launch_matvec<T>(k, v.x, v.u, s, &st->mv_p_on);
-    k_pk_begin<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.f, v.x, v.u, cm, part, tk, st, c.n);
-    k_pk_dir<T><<<c.eb, NTHREADS, 0, s>>>(cm, v.g, v.t, st, c.n);
+    launch_pdl(k_pk_begin<T>, c.rb, NTHREADS, 0, s, v.p, v.g, (const T*)v.f, v.x, (const T*)v.u, cm, part, tk, st,
+               c.n);
+    launch_pdl(k_pk_dir<T>, c.eb, NTHREADS, 0, s, (const uint8_t*)cm, (const T*)v.g, v.t, (const SolveState*)st, c.n);
     launch_matvec<T>(k, v.t, v.r, s, &st->mv_t_on);
-    k_pk_rt<T><<<sizeof(T) == 4 ? c.rb6 : c.rb, NTHREADS, 0, s>>>(cm, v.g, v.t, v.r, part, tk, st, c.n);
-    k_pk_update<T><<<c.rb, NTHREADS, 0, s>>>(v.p, v.g, v.t, v.r, v.x, v.f, part, tk, st, c.n);
+    launch_pdl(k_pk_rt<T>, sizeof(T) == 4 ? c.rb6 : c.rb, NTHREADS, 0, s, (const uint8_t*)cm, (const T*)v.g,
+               (const T*)v.t, (const T*)v.r, part, tk, st, c.n);
+    launch_pdl(k_pk_update<T>, c.rb, NTHREADS, 0, s, v.p, v.g, (const T*)v.t, (const T*)v.r, v.x, (const T*)v.f,
+               part, tk, st, c.n);
     note_launches(4);
   }
 }
@@ -1042,9 +1052,10 @@ void lin_chunk_launches(bem_kernel_s* k, const uint8_t* C, cudaStream_t s) {
   unsigned int* tk = k->ws.ticket;
   for (int it = 0; it < CHUNK; ++it) {
     launch_matvec<T>(k, v.t, v.g, s, &st->mv_t_on);
-    k_lin_alpha<T><<<c.rb, NTHREADS, 0, s>>>(v.t, v.g, v.r, C, part, tk, st, c.n);
-    k_lin_update<T><<<c.rb, NTHREADS, 0, s>>>(v.x, v.r, v.t, v.g, C, part, tk, st, c.n);
-    k_lin_dir<T><<<c.eb, NTHREADS, 0, s>>>(v.r, v.t, C, st, c.n);
+    launch_pdl(k_lin_alpha<T>, c.rb, NTHREADS, 0, s, (const T*)v.t, (const T*)v.g, (const T*)v.r, C, part, tk, st,
+               c.n);
+    launch_pdl(k_lin_update<T>, c.rb, NTHREADS, 0, s, v.x, v.r, (const T*)v.t, (const T*)v.g, C, part, tk, st, c.n);
+    launch_pdl(k_lin_dir<T>, c.eb, NTHREADS, 0, s, (const T*)v.r, v.t, C, (const SolveState*)st, c.n);
     note_launches(3);
   }
 }

@@ -25,6 +25,7 @@ class RadixCache:
         self.path = path
         self.device = device
         self.choice = {}
+        self.by_size = {}   # grid size -> the radices last applied to a handle of that size
         if path is not None and os.path.exists(path):
             try:
                 with open(path) as fh:
@@ -38,6 +39,7 @@ class RadixCache:
     def apply(self, k, stream=None):
         if self.fixed is not None:
             k.set_radix(*self.fixed, stream=stream)
+            self.by_size[k.N] = self.fixed
             return self.fixed
         key = self.key(k)
         if key in self.choice:
@@ -45,6 +47,7 @@ class RadixCache:
         else:
             self.choice[key] = tuple(k.autotune(reps=5, stream=stream))
             self._write()
+        self.by_size[k.N] = self.choice[key]
         return self.choice[key]
 
     def _write(self):

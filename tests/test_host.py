@@ -196,9 +196,11 @@ def test_radix_cache_tunes_once_per_size(bench):
     assert rc.apply(a) == (4, 3) and a.calls == [("tune",)]
     assert rc.apply(b) == (4, 3) and b.calls == [("set", 4, 3)]
     assert rc.apply(c) == (4, 3) and c.calls == [("tune",)]
+    assert rc.by_size == {512: (4, 3), 1024: (4, 3)}   # what the bench line reports per size
     fixed = bench.RadixCache(fixed=(4, 4))
     d = _FakeKernel(512)
     assert fixed.apply(d) == (4, 4) and d.calls == [("set", 4, 4)]
+    assert fixed.by_size == {512: (4, 4)}
 
 
 def test_radix_cache_file_is_reused(tmp_path):
