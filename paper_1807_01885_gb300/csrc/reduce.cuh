@@ -20,6 +20,7 @@ template <typename T> struct Acc;
 template <> struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_sq(double x) { s += x * x; }
   __device__ __forceinline__ void add4(const double (&x)[4]) { s += (x[0] + x[1]) + (x[2] + x[3]); }
   __device__ __forceinline__ void combine(const Acc& o) { s += o.s; }
   __device__ __forceinline__ Acc shfl_down(int o) const {
@@ -43,6 +44,14 @@ template <> struct Acc<float> {
     const float bp = t - hi;
     lo += (hi - (t - bp)) + (x - bp);
     hi = t;
+  }
+  // x^2 with its rounding error (TwoProduct by fma) added in: the sum of squares keeps
+  // the pair's precision even when the squares are large against their spread
+  __device__ __forceinline__ void add_sq(float x) {
+    const float q = x * x;
+    const float e = fmaf(x, x, -q);
+    add(q);
+    lo += e;
   }
   // four terms of one 16-byte group: summed pairwise in float (each term carries its
   // own float rounding already), then one compensated addition

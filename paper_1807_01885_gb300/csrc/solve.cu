@@ -220,19 +220,24 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T
       st4(dp, i4, xv);
     }
     stm4(cm, i4, pv);
-    T sg[4], sgg[4], suu[4], sp[4], sc[4];
+    T sg[4], suu[4], sp[4], sc[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const bool in = pv[e] > (T)0;
       const T ui = gv[e] - (fv[e] - dT);
       sg[e] = in ? gv[e] : (T)0;
-      sgg[e] = in ? gv[e] * gv[e] : (T)0;
       suu[e] = in ? ui * ui : (T)0;
       sp[e] = in ? pv[e] : (T)0;
       sc[e] = in ? (T)1 : (T)0;
     }
-    ag.add4(sg);
-    agg.add4(sgg);
+    // the gap sums element by element, with exact squares: under force control G is
+    // their difference sum g^2 - 2 gbar sum g + n gbar^2, which cancels when the gaps
+    // share a large common offset (a depth far off after a replacement, say)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ag.add(sg[e]);
+      agg.add_sq(sg[e]);
+    }
     auu.add4(suu);
     ap.add4(sp);
     cnt.add4(sc);
@@ -253,7 +258,13 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T
     const double gbar = (st->control == BEM_CTRL_FORCE) ? (double)(T)(tot[0] / tot[1]) : 0.0;
     st->uscale = sqrt(tot[3] / tot[1]);
     st->pscale = tot[4] / tot[1];
-    const double G = (st->control == BEM_CTRL_FORCE) ? fmax(tot[2] - tot[1] * gbar * gbar, 0.0) : tot[2];
+    // sum over Ic of (g - gbar)^2 with the shift actually applied (gbar in the path
+    // precision), not the mean: written out, so that a rounded shift leaves no error
+    double G = tot[2];
+    if (st->control == BEM_CTRL_FORCE) {
+      G = tot[2] - 2.0 * gbar * tot[0] + tot[1] * gbar * gbar;
+      if (isfinite(G)) G = fmax(G, 0.0);
+    }
     st->gbar = gbar;
     st->G = G;
     st->res = (tot[3] > 0.0) ? sqrt(G / tot[3]) : 0.0;
@@ -278,7 +289,8 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T
       finish(st, BEM_ENOCONV);
       return;
     }
-    st->beta = st->flag * G / st->Gold;
+    // (a previous residual of zero, a level gap, leaves nothing to keep conjugate to)
+    st->beta = st->Gold > 0.0 ? st->flag * G / st->Gold : 0.0;
     st->Gold = G;
     st->d += gbar;
   }
@@ -312,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 1) k_pk_rt(cons
   pdl_enter();
   if (st->done) return;
   const T gbar = (T)st->gbar;
-  Acc<T> art, ar, at, agt;
+  Acc<T> art, ar, at, agt, aab;
   VEC_LOOP(i4, n) {
     T gv[4], tv[4], rv[4];
     bool in[4];
@@ -320,31 +332,43 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 1) k_pk_rt(cons
     ld4(g, i4, gv);
     ld4(t, i4, tv);
     ld4(r, i4, rv);
-    T srt[4], sr[4], st_[4], sgt[4];
+    T srt[4], sr[4], st_[4], sgt[4], sab[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       srt[e] = in[e] ? rv[e] * tv[e] : (T)0;
       sr[e] = in[e] ? rv[e] : (T)0;
       st_[e] = in[e] ? tv[e] : (T)0;
       sgt[e] = in[e] ? (gv[e] - gbar) * tv[e] : (T)0;
+      sab[e] = in[e] ? fabs(rv[e] * tv[e]) : (T)0;
     }
     art.add4(srt);
     ar.add4(sr);
     at.add4(st_);
     agt.add4(sgt);
+    aab.add4(sab);
   }
-  Acc<T> v[4] = {art, ar, at, agt};
-  double tot[4];
-  if (grid_reduce<4>(v, partials, ticket, tot)) {
+  Acc<T> v[5] = {art, ar, at, agt, aab};
+  double tot[5];
+  if (grid_reduce<5>(v, partials, ticket, tot)) {
     const double rbar = (st->control == BEM_CTRL_FORCE) ? tot[1] / (double)st->n_c : 0.0;
     const double den = tot[0] - rbar * tot[2];
+    // rounding level of the curvature: the operator product's relative error (float
+    // FFT ~1e-6, double ~1e-14) times the sizes of the terms it is formed from
+    const double noise = (sizeof(T) == 4 ? 1e-5 : 1e-12) * (tot[4] + fabs(rbar * tot[2]));
     double tau = 0.0;
     if (den == 0.0 && tot[3] == 0.0) {
       // the gap is exactly level on the contact set (a symmetric set under force
       // control): the direction is zero and no step is taken, as in the oracle
+    } else if (!isfinite(den) || !isfinite(tot[3]) || den < -noise) {
+      finish(st, BEM_ENAN);   // non-finite, or a curvature clearly negative: K is indefinite on the set
+      return;
+    } else if (!(den > noise)) {
+      // a curvature within the product's rounding: the direction is at the noise floor
+      // of the path precision; no step is taken and the next direction restarts
+      st->restart_next = 1;
     } else {
       tau = tot[3] / den;
-      if (!(den > 0.0) || !isfinite(tau)) {
+      if (!isfinite(tau)) {
         finish(st, BEM_ENAN);
         return;
       }
@@ -469,7 +493,7 @@ __global__ void k_final_stats(const T* __restrict__ p, const T* __restrict__ u, 
       const T ui = u[i];
       const T gi = ui + (f[i] - dT);
       ag.add(gi);
-      agg.add(gi * gi);
+      agg.add_sq(gi);
       auu.add(ui * ui);
       cnt.add((T)1);
     }

@@ -1,0 +1,86 @@
+"""Seeded random sweep of contact solves against the oracle: grid size, coating
+(thickness, modulus ratio, Poisson ratios, rigid or elastic base), DC rule, indenter
+(sphere, rough surface, flat punch), control (depth or force), precision and
+warm start drawn per case.  Each case is either solved by both sides (pressure,
+force and contact count compared at the precision's tolerance) or refused by both:
+an operator that the oracle finds indefinite on the contact set must end the GPU
+solve with BEM_ENAN, never with a pressure."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import contact, operator
+from paper_1807_01885_gb300 import bem, inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = 40
+
+
+def draw(i):
+    rng = np.random.default_rng(7100 + i)
+    N = int(rng.choice([8, 16, 32, 64]))
+    delta = 1.0 / N
+    h = delta * float(np.exp(rng.uniform(np.log(0.5), np.log(40.0))))
+    E1 = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+    E2 = float("inf") if rng.random() < 0.2 else 1.0
+    nu1, nu2 = (float(x) for x in rng.uniform(0.15, 0.48, size=2))
+    dc_mode = int(rng.random() < 0.3)
+    shape = str(rng.choice(["sphere", "rough", "punch"]))
+    control = str(rng.choice(["depth", "force"]))
+    precision = str(rng.choice(["fp64", "fp32"]))
+    warm = bool(rng.random() < 0.3)
+    if shape == "sphere":
+        f = inputs.sphere_height(N, delta, 1.0)
+    elif shape == "rough":
+        f = inputs.rough_surface(N, delta, seed=9000 + i)
+    else:
+        f = inputs.flat_punch_height(N, delta, 0.25)
+    return dict(N=N, delta=delta, h=h, E1=E1, E2=E2, nu1=nu1, nu2=nu2, dc_mode=dc_mode, shape=shape,
+                control=control, precision=precision, warm=warm, f=f, rng=rng)
+
+
+@pytest.mark.parametrize("i", range(CASES))
+def test_random_case_matches_oracle(cuda, i):
+    c = draw(i)
+    N, delta, f = c["N"], c["delta"], c["f"]
+    Kg = operator.khat_grid(N, delta, c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"], c["dc_mode"])
+    mv = lambda p: operator.matvec_fft(Kg, p)
+    # a load that presses a few to most cells into contact: the force of a uniform
+    # depth of a quarter of the height range over the window's mean compliance
+    span = float(f.max() - f.min())
+    d = 1e-3 * N * delta if c["shape"] == "punch" else 0.25 * span
+    if c["control"] == "depth":
+        target = d
+    else:
+        u1 = mv(np.ones((N, N)))
+        target = float(d / u1.mean() * (N * delta) ** 2) * 0.5
+    p0 = None
+    if c["warm"]:
+        p0 = np.abs(c["rng"].standard_normal((N, N))) * (target if c["control"] == "force" else 1.0)
+    refused = False
+    try:
+        ref = contact.solve_nonadhesive(mv, f, delta, c["control"], target, tol=1e-12, p0=p0)
+    except contact.NotPositiveDefinite:
+        refused = True
+    dt = torch.float64 if c["precision"] == "fp64" else torch.float32
+    tol = 1e-12 if c["precision"] == "fp64" else 1e-8
+    with bem.Kernel(N, delta, c["h"], c["E1"], c["nu1"], c["E2"], c["nu2"], precision=c["precision"],
+                    dc_mode=c["dc_mode"]) as k:
+        pi = None if p0 is None else torch.tensor(p0, dtype=dt, device=cuda)
+        if refused:
+            with pytest.raises(bem.BemError) as e:
+                k.solve(torch.tensor(f, dtype=dt, device=cuda), c["control"], target, tol=tol, max_iter=20000,
+                        p_init=pi)
+            assert e.value.status == bem.BEM_ENAN, c
+            return
+        p, res = k.solve(torch.tensor(f, dtype=dt, device=cuda), c["control"], target, tol=tol, max_iter=20000,
+                         p_init=pi)
+    assert res["status"] == 0, (res, {k_: v for k_, v in c.items() if k_ not in ("f", "rng")})
+    p = p.double().cpu().numpy()
+    tp, tf = (1e-9, 1e-9) if c["precision"] == "fp64" else (2e-3, 1e-5)
+    scale = np.linalg.norm(ref["p"])
+    assert np.linalg.norm(p - ref["p"]) <= tp * scale + 1e-300, c["precision"]
+    assert res["force"] == pytest.approx(ref["force"], rel=tf, abs=1e-300)
+    if c["precision"] == "fp64":   # cells at the contact edge may carry p ~ 0 on either side
+        assert abs(res["n_contact"] - ref["n_contact"]) <= max(1, 0.01 * ref["n_contact"])
