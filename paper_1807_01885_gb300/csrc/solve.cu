@@ -233,10 +233,12 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) k_pk_begin(T
     // the gap sums element by element, with exact squares: under force control G is
     // their difference sum g^2 - 2 gbar sum g + n gbar^2, which cancels when the gaps
     // share a large common offset (a depth far off after a replacement, say)
+    if (sc[0] + sc[1] + sc[2] + sc[3] > (T)0) {   // groups without a contact cell add nothing
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      ag.add(sg[e]);
-      agg.add_sq(sg[e]);
+      for (int e = 0; e < 4; ++e) {
+        ag.add(sg[e]);
+        agg.add_sq(sg[e]);
+      }
     }
     auu.add4(suu);
     ap.add4(sp);
