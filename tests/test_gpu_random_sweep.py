@@ -84,3 +84,60 @@ def test_random_case_matches_oracle(cuda, i):
     assert res["force"] == pytest.approx(ref["force"], rel=tf, abs=1e-300)
     if c["precision"] == "fp64":   # cells at the contact edge may carry p ~ 0 on either side
         assert abs(res["n_contact"] - ref["n_contact"]) <= max(1, 0.01 * ref["n_contact"])
+
+
+STACK_CASES = 16
+
+
+def draw_variant(i):
+    """A coating stack of two or three layers (dc_mode 1) or the open-plane operator of a
+    homogeneous half-space, with a random indenter, control and precision."""
+    rng = np.random.default_rng(7700 + i)
+    N = int(rng.choice([8, 16, 32, 64]))
+    delta = 1.0 / N
+    kind = "open" if i % 4 == 3 else "stack"
+    layers = [(delta * float(np.exp(rng.uniform(np.log(0.5), np.log(10.0)))),
+               float(np.exp(rng.uniform(np.log(0.2), np.log(5.0)))), float(rng.uniform(0.15, 0.45)))
+              for _ in range(int(rng.integers(2, 4)))]
+    E_sub = float("inf") if rng.random() < 0.25 else 1.0
+    nu_sub = float(rng.uniform(0.15, 0.45))
+    shape = str(rng.choice(["sphere", "rough"]))
+    control = str(rng.choice(["depth", "force"]))
+    precision = str(rng.choice(["fp64", "fp32"]))
+    f = inputs.sphere_height(N, delta, 1.0) if shape == "sphere" else inputs.rough_surface(N, delta, seed=9500 + i)
+    return dict(N=N, delta=delta, kind=kind, layers=layers, E_sub=E_sub, nu_sub=nu_sub, E=layers[0][1],
+                nu=layers[0][2], shape=shape, control=control, precision=precision, f=f)
+
+
+@pytest.mark.parametrize("i", range(STACK_CASES))
+def test_random_stack_or_open_case_matches_oracle(cuda, i):
+    from oracle import influence
+    c = draw_variant(i)
+    N, delta, f = c["N"], c["delta"], c["f"]
+    if c["kind"] == "stack":
+        Kg = operator.khat_grid_layers(N, delta, c["layers"], c["E_sub"], c["nu_sub"], dc_mode=1)
+        mv = lambda p: operator.matvec_fft(Kg, p)
+    else:
+        G = influence.influence_love(N, delta, c["E"], c["nu"])
+        mv = lambda p: influence.matvec_fft_np(G, p)
+    d = 0.25 * float(f.max() - f.min())
+    if c["control"] == "depth":
+        target = d
+    else:
+        target = float(d / mv(np.ones((N, N))).mean() * (N * delta) ** 2) * 0.5
+    ref = contact.solve_nonadhesive(mv, f, delta, c["control"], target, tol=1e-12)
+    dt = torch.float64 if c["precision"] == "fp64" else torch.float32
+    tol = 1e-12 if c["precision"] == "fp64" else 1e-8
+    if c["kind"] == "stack":
+        k = bem.Kernel(N, delta, layers=c["layers"], E2=c["E_sub"], nu2=c["nu_sub"], precision=c["precision"],
+                       dc_mode=1)
+    else:
+        k = bem.Kernel(N, delta, np.inf, c["E"], c["nu"], c["E"], c["nu"], precision=c["precision"],
+                       op_kind=bem.BEM_OP_OPEN)
+    with k:
+        p, res = k.solve(torch.tensor(f, dtype=dt, device=cuda), c["control"], target, tol=tol, max_iter=20000)
+    assert res["status"] == 0, (res, c["kind"], c["precision"])
+    p = p.double().cpu().numpy()
+    tp, tf = (1e-9, 1e-9) if c["precision"] == "fp64" else (2e-3, 1e-5)
+    assert np.linalg.norm(p - ref["p"]) <= tp * np.linalg.norm(ref["p"]), (c["kind"], c["precision"])
+    assert res["force"] == pytest.approx(ref["force"], rel=tf)
