@@ -111,3 +111,29 @@ def test_matvec_is_deterministic(cuda):
         a = k.matvec(pr).clone()
         b = k.matvec(pr).clone()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("N,precision", [(64, "fp64"), (64, "fp32"), (2048, "fp32")])
+def test_back_to_back_products_equal_isolated_ones(cuda, N, precision):
+    """The passes of consecutive products are launched with programmatic dependent
+    launch (each may be scheduled while its predecessor finishes).  A chain of products
+    on one stream without any synchronisation, u_{i+1} = K u_i (every product reading
+    what the one before wrote), equals the same chain with a full device
+    synchronisation after every product, bit for bit."""
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    s = torch.cuda.Stream(device=cuda)
+    with bem.Kernel(N, 1.0 / N, 2.0 / N, 3.0, 0.3, 1.0, 0.4, precision=precision) as k:
+        x0 = torch.tensor(np.random.default_rng(N).random((N, N)), dtype=dt, device=cuda)
+        with torch.cuda.stream(s):
+            chain = [x0]
+            for _ in range(12):
+                chain.append(k.matvec(chain[-1], torch.empty_like(x0), stream=s))
+            s.synchronize()
+            ref = [x0]
+            for _ in range(12):
+                torch.cuda.synchronize()
+                ref.append(k.matvec(ref[-1], torch.empty_like(x0), stream=s))
+                torch.cuda.synchronize()
+    assert all(bool(torch.isfinite(a).all()) for a in chain)
+    for a, b in zip(chain, ref):
+        assert torch.equal(a, b)
