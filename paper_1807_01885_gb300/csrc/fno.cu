@@ -30,6 +30,48 @@ using bf16 = __nv_bfloat16;
 __device__ __forceinline__ float b2f(bf16 x) { return __bfloat162float(x); }
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// gelu of two values at once on packed .f32x2 arithmetic (the fused layer and
+// projection epilogues), with erf by Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7):
+// 1 + erf(u) = 2 - y for u >= 0 and y for u < 0, y = t P(t) e^{-u^2} = erfc(|u|),
+// t = 1 / (1 + p |u|).  The polynomial and the products run two lanes per
+// instruction; the reciprocal and the exponential stay per value (MUFU).
+typedef unsigned long long g2x;
+__device__ __forceinline__ g2x gpk(float a, float b) {
+  g2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void gup(g2x v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ g2x gfma(g2x a, g2x b, g2x c) {
+  g2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ g2x gmul(g2x a, g2x b) {
+  g2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ g2x gsplat(float a) { return gpk(a, a); }
+__device__ __forceinline__ void gelu2(float& z0, float& z1) {
+  const g2x z = gpk(z0, z1);
+  const g2x u = gmul(z, gsplat(0.70710678118654752f));
+  const g2x a = u & 0x7fffffff7fffffffull;   // |u| in both lanes
+  float d0, d1;
+  gup(gfma(a, gsplat(0.3275911f), gsplat(1.f)), d0, d1);
+  const g2x t = gpk(__fdividef(1.f, d0), __fdividef(1.f, d1));
+  g2x y = gfma(t, gsplat(1.061405429f), gsplat(-1.453152027f));
+  y = gfma(t, y, gsplat(1.421413741f));
+  y = gfma(t, y, gsplat(-0.284496736f));
+  y = gfma(t, y, gsplat(0.254829592f));
+  float q0, q1;
+  gup(gmul(a, a), q0, q1);
+  y = gmul(gmul(t, y), gpk(__expf(-q0), __expf(-q1)));
+  float y0, y1, u0, u1;
+  gup(y, y0, y1);
+  gup(u, u0, u1);
+  gup(gmul(gmul(z, gsplat(0.5f)), gpk(u0 >= 0.f ? 2.f - y0 : y0, u1 >= 0.f ? 2.f - y1 : y1)), z0, z1);
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
@@ -639,8 +681,10 @@ __global__ void __launch_bounds__(128) k_layer_tc(const float* __restrict__ V, c
           if (oka) zb[oo + ya] = va;
           if (okb) zb[oo + yb] = vb2;
         }
-        if (oka) ub[oo + ya] = gelu ? gelu_f(va) : va;
-        if (okb) ub[oo + yb] = gelu ? gelu_f(vb2) : vb2;
+        float wa = va, wb = vb2;
+        if (gelu) gelu2(wa, wb);
+        if (oka) ub[oo + ya] = wa;
+        if (okb) ub[oo + yb] = wb;
       }
     }
   };
@@ -797,8 +841,10 @@ __global__ void __launch_bounds__(128, 4) k_layer_tc_pipe(const float* __restric
           zb[oo + ya] = va;
           zb[oo + yb] = vb2;
         }
-        ub[oo + ya] = gelu ? gelu_f(va) : va;
-        ub[oo + yb] = gelu ? gelu_f(vb2) : vb2;
+        float wa = va, wb = vb2;
+        if (gelu) gelu2(wa, wb);
+        ub[oo + ya] = wa;
+        ub[oo + yb] = wb;
       }
     }
   }
@@ -875,8 +921,11 @@ __global__ void __launch_bounds__(128) k_proj_tc(const float* __restrict__ X, in
         mma_bf16(acc, ah[kb], wf[kb][nt][0], wf[kb][nt][1]);
         mma_bf16(acc, al[kb], wf[kb][nt][0], wf[kb][nt][1]);
       }
-      sa += qw[nt][0] * gelu_f(acc[0] + qb[nt][0]) + qw[nt][1] * gelu_f(acc[1] + qb[nt][1]);
-      sb += qw[nt][0] * gelu_f(acc[2] + qb[nt][0]) + qw[nt][1] * gelu_f(acc[3] + qb[nt][1]);
+      float h0 = acc[0] + qb[nt][0], h1 = acc[1] + qb[nt][1], h2 = acc[2] + qb[nt][0], h3 = acc[3] + qb[nt][1];
+      gelu2(h0, h1);
+      gelu2(h2, h3);
+      sa += qw[nt][0] * h0 + qw[nt][1] * h1;
+      sb += qw[nt][0] * h2 + qw[nt][1] * h3;
     }
     sa += __shfl_xor_sync(0xffffffffu, sa, 1);
     sa += __shfl_xor_sync(0xffffffffu, sa, 2);
