@@ -475,64 +475,83 @@ __global__ void __launch_bounds__(128) k_idft_y_tc(const float* __restrict__ A, 
   }
 }
 
-// Pointwise (1x1) layer on the tensor cores: for 16 pixels of one sample (a warp)
+// Pointwise (1x1) layer on the tensor cores: for 16 pixels of one sample (a tile)
 // D (pixels x cout) = X^T (pixels x cin) W^T (cin x cout), the activations split into
 // bf16 hi + lo (two mma.sync each), the weights used as they are stored (bf16).  Same
 // result as k_pw: Y[b][o][p] = bias[o] + sum_c W[o][c] X[b][c][p] (+ Y when ACCUM),
 // Yact = gelu(Y) when GELU; TRANS uses W^T.  KT = ceil(cin/16) k-blocks, NT =
-// ceil(cout/8) n-tiles (cout <= 64).
+// ceil(cout/8) n-tiles (cout <= 64).  Each warp loads its weight fragments once and
+// runs kPwTiles consecutive tiles.
+constexpr int kPwTiles = 8;
 template <int KT, int NT, bool TRANS, bool ACCUM, bool GELU>
 __global__ void __launch_bounds__(128) k_pw_tc(const float* __restrict__ X, int cin, const bf16* __restrict__ Wt,
                                                const bf16* __restrict__ bias, float* __restrict__ Y,
                                                float* __restrict__ Yact, int cout, size_t P) {
   const int lane = threadIdx.x % 32, g = lane / 4, t = lane % 4;
   const int b = blockIdx.y;
-  const size_t p0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * 16;
-  if (p0 >= P) return;
-  const size_t pa = p0 + g, pb = p0 + g + 8;
-  const bool oka = pa < P, okb = pb < P;
-  const float* xb = X + (size_t)b * cin * P;
-  auto xv = [&](int c, size_t p, bool ok) -> float { return (ok && c < cin) ? xb[(size_t)c * P + p] : 0.f; };
-  unsigned ah[KT][4], al[KT][4];
-#pragma unroll
-  for (int kb = 0; kb < KT; ++kb) {
-    const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
-    split2(xv(c0, pa, oka), xv(c0 + 1, pa, oka), ah[kb][0], al[kb][0]);
-    split2(xv(c0, pb, okb), xv(c0 + 1, pb, okb), ah[kb][1], al[kb][1]);
-    split2(xv(c1, pa, oka), xv(c1 + 1, pa, oka), ah[kb][2], al[kb][2]);
-    split2(xv(c1, pb, okb), xv(c1 + 1, pb, okb), ah[kb][3], al[kb][3]);
-  }
+  const size_t tiles = (P + 15) / 16;
+  const size_t tile0 = ((size_t)blockIdx.x * 4 + threadIdx.x / 32) * kPwTiles;
+  if (tile0 >= tiles) return;
   // B[c][o] = W[o][c]: TRANS reads Wt[c][o] (stored [cin][cout]), else Wt[o][c]
   auto wbits = [&](int c, int o) -> unsigned {
     if (c >= cin || o >= cout) return 0u;
     const bf16 w = TRANS ? Wt[(size_t)c * cout + o] : Wt[(size_t)o * cin + c];
     return (unsigned)__bfloat16_as_ushort(w);
   };
+  unsigned wf[KT][NT][2];
 #pragma unroll
-  for (int nt = 0; nt < NT; ++nt) {
-    const int n = 8 * nt + g;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int kb = 0; kb < KT; ++kb)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int n = 8 * nt + g, c0 = 16 * kb + 2 * t, c1 = c0 + 8;
+      wf[kb][nt][0] = wbits(c0, n) | (wbits(c0 + 1, n) << 16);
+      wf[kb][nt][1] = wbits(c1, n) | (wbits(c1 + 1, n) << 16);
+    }
+  float bv[NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int o = 8 * nt + 2 * t + e;
+      bv[nt][e] = (bias != nullptr && o < cout) ? b2f(bias[o]) : 0.f;
+    }
+  const float* xb = X + (size_t)b * cin * P;
+  const size_t tile1 = tile0 + kPwTiles < tiles ? tile0 + kPwTiles : tiles;
+  for (size_t tile = tile0; tile < tile1; ++tile) {
+    const size_t pa = tile * 16 + g, pb = pa + 8;
+    const bool oka = pa < P, okb = pb < P;
+    auto xv = [&](int c, size_t p, bool ok) -> float { return (ok && c < cin) ? xb[(size_t)c * P + p] : 0.f; };
+    unsigned ah[KT][4], al[KT][4];
 #pragma unroll
     for (int kb = 0; kb < KT; ++kb) {
       const int c0 = 16 * kb + 2 * t, c1 = c0 + 8;
-      const unsigned b0 = wbits(c0, n) | (wbits(c0 + 1, n) << 16);
-      const unsigned b1 = wbits(c1, n) | (wbits(c1 + 1, n) << 16);
-      mma_bf16(acc, ah[kb], b0, b1);
-      mma_bf16(acc, al[kb], b0, b1);
+      split2(xv(c0, pa, oka), xv(c0 + 1, pa, oka), ah[kb][0], al[kb][0]);
+      split2(xv(c0, pb, okb), xv(c0 + 1, pb, okb), ah[kb][1], al[kb][1]);
+      split2(xv(c1, pa, oka), xv(c1 + 1, pa, oka), ah[kb][2], al[kb][2]);
+      split2(xv(c1, pb, okb), xv(c1 + 1, pb, okb), ah[kb][3], al[kb][3]);
     }
-    // acc[0], acc[1]: pixel pa, outputs o0, o0 + 1; acc[2], acc[3]: pixel pb
-    const int o0 = 8 * nt + 2 * t;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int o = o0 + (e & 1);
-      const size_t p = (e < 2) ? pa : pb;
-      const bool ok = (e < 2) ? oka : okb;
-      if (!ok || o >= cout) continue;
-      float v = acc[e] + (bias != nullptr ? b2f(bias[o]) : 0.f);
-      float* y = Y + ((size_t)b * cout + o) * P + p;
-      if (ACCUM) v += *y;
-      *y = v;
-      if (GELU) Yact[((size_t)b * cout + o) * P + p] = gelu_f(v);
+    for (int nt = 0; nt < NT; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kb = 0; kb < KT; ++kb) {
+        mma_bf16(acc, ah[kb], wf[kb][nt][0], wf[kb][nt][1]);
+        mma_bf16(acc, al[kb], wf[kb][nt][0], wf[kb][nt][1]);
+      }
+      // acc[0], acc[1]: pixel pa, outputs o0, o0 + 1; acc[2], acc[3]: pixel pb
+      const int o0 = 8 * nt + 2 * t;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int o = o0 + (e & 1);
+        const size_t p = (e < 2) ? pa : pb;
+        const bool ok = (e < 2) ? oka : okb;
+        if (!ok || o >= cout) continue;
+        float v = acc[e] + bv[nt][e & 1];
+        float* y = Y + ((size_t)b * cout + o) * P + p;
+        if (ACCUM) v += *y;
+        *y = v;
+        if (GELU) Yact[((size_t)b * cout + o) * P + p] = gelu_f(v);
+      }
     }
   }
 }
@@ -1382,7 +1401,8 @@ bem_status ensure(bem_fno_s* f, int B, int N, bool train, cudaStream_t s) {
 template <int KT, int NT, bool TRANS, bool ACCUM, bool GELU>
 void pw_tc_launch(const float* X, int cin, const bf16* Wt, const bf16* bias, float* Y, float* Yact, int cout,
                   size_t P, int B, cudaStream_t s) {
-  const dim3 grid((unsigned)((P + 63) / 64), B);
+  const size_t warps = ((P + 15) / 16 + kPwTiles - 1) / kPwTiles;
+  const dim3 grid((unsigned)((warps + 3) / 4), B);
   k_pw_tc<KT, NT, TRANS, ACCUM, GELU><<<grid, 128, 0, s>>>(X, cin, Wt, bias, Y, Yact, cout, P);
 }
 
