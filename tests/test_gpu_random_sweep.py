@@ -141,3 +141,49 @@ def test_random_stack_or_open_case_matches_oracle(cuda, i):
     tp, tf = (1e-9, 1e-9) if c["precision"] == "fp64" else (2e-3, 1e-5)
     assert np.linalg.norm(p - ref["p"]) <= tp * np.linalg.norm(ref["p"]), (c["kind"], c["precision"])
     assert res["force"] == pytest.approx(ref["force"], rel=tf)
+
+
+def test_random_mixed_batch_equals_single_solves(cuda):
+    """One bem_solve_batch call over a seeded mix: grid sizes 16 to 128, both precisions,
+    depth and force control, cold and warm starts, one adhesive step, and an instance
+    whose iteration limit is too small.  Every instance equals its own single solve bit
+    for bit (pressure, iterations, products, status)."""
+    rng = np.random.default_rng(4242)
+    ks, probs, outs, singles, keep = [], [], [], [], []
+    for i in range(14):
+        N = int(rng.choice([16, 32, 64, 128]))
+        delta = 1.0 / N
+        precision = str(rng.choice(["fp64", "fp32"]))
+        dt = torch.float64 if precision == "fp64" else torch.float32
+        E1 = float(np.exp(rng.uniform(np.log(0.3), np.log(3.0))))
+        k = bem.Kernel(N, delta, delta * float(rng.uniform(1, 10)), E1, 0.3, 1.0, 0.35, precision=precision,
+                       dc_mode=1)
+        f = torch.tensor(inputs.rough_surface(N, delta, seed=600 + i), dtype=dt, device=cuda)
+        span = float(f.max() - f.min())
+        adhesive = i == 5
+        control = "depth" if (adhesive or rng.random() < 0.5) else "force"
+        target = 0.25 * span if control == "depth" else 1e-3 * span
+        p0 = torch.tensor(np.abs(rng.standard_normal((N, N))) * 1e-3, dtype=dt, device=cuda) if rng.random() < 0.3 \
+            else None
+        max_iter = 3 if i == 9 else 20000
+        dg = 1e-4 if adhesive else 0.0
+        mask = torch.zeros((N, N), dtype=torch.uint8, device=cuda) if adhesive else None
+        p, r = k.solve(f, control, target, dgamma=dg, tol=1e-10 if precision == "fp64" else 1e-8, max_iter=max_iter,
+                       p_init=p0, contact_mask=None if mask is None else mask.clone())
+        singles.append((p.clone(), r))
+        ctrl = bem.BEM_CTRL_DEPTH if control == "depth" else bem.BEM_CTRL_FORCE
+        bmask = None if mask is None else mask.clone()   # kept alive below: the problem holds its address
+        probs.append(bem.make_problem(f, ctrl, target, dg, 1e-10 if precision == "fp64" else 1e-8, max_iter, p0,
+                                      bmask))
+        keep.append((f, p0, bmask))
+        ks.append(k)
+        outs.append(torch.empty_like(f))
+    st, res = bem.bem_solve_batch([k.handle for k in ks], probs, outs)
+    assert st in (bem.BEM_OK, bem.BEM_ENOCONV)
+    for (p, r), o, rb in zip(singles, outs, res):
+        assert rb["status"] == r["status"]
+        assert rb["iters"] == r["iters"] and rb["matvecs"] == r["matvecs"]
+        assert torch.equal(p, o)
+    assert res[9]["status"] == bem.BEM_ENOCONV
+    for k in ks:
+        k.close()
