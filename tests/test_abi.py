@@ -29,6 +29,20 @@ def test_library_exports_every_declared_symbol(bemlib):
     assert bem.bem_version() == 100
 
 
+def test_status_codes_match_header():
+    """Every bem_status value of include/bem.h has the same number and name in the
+    binding (statuses are compared by value on both sides of the ABI)."""
+    from paper_1807_01885_gb300 import bem
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    body = re.search(r"typedef enum \{(.*?)\} bem_status;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    codes = {name: int(val) for name, val in re.findall(r"(BEM_[A-Z]+)\s*=\s*(\d+)", body)}
+    assert codes and len(codes) == len(bem.STATUS_NAMES)
+    for name, val in codes.items():
+        assert getattr(bem, name) == val, name
+        assert bem.STATUS_NAMES[val] == name
+
+
 def test_struct_layouts_match_header():
     from paper_1807_01885_gb300 import bem
     assert ctypes.sizeof(bem.KernelDesc) == 4 * 4 + 6 * 8
